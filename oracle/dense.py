@@ -1,0 +1,112 @@
+"""Brute-force dense restatement of Algorithm 4.1 for tiny grids (pins `sgf`).
+
+Everything lives in explicit n x n matrices with global index sets ("slots"):
+the current matrix M and the accumulated factor F = G1 B1 G2 B2 ... so that
+the approximation after k levels is A_k = F M F^T (Sec. 2.1, Sec. 6).
+
+* Elimination of interior I with slots s (Eq. (elimination)): G = I_n with
+  G[s, s] = L and G[rest, s] = M[rest, s] L^{-T}; M becomes identity on s and
+  the Schur complement on the rest; F <- F G.
+* Compression of B (Eq. (M')): with M_BB = L L^T, M^ = L^{-1} M[s, others],
+  Phi_X for every node taken straight from its definition Eq. (PhiD),
+  Phi_X = (F^T Pi_X)[active slots of X] with Pi_X the cell's basis on all of
+  its unknowns (Eq. (def:PiB)) - no update or merge formula is used;
+  N = [L^T Phi_B, M^_X Phi_X for every other node X] (zero blocks give zero
+  columns), pivoted QR, rank r; if r < m: F <- F diag(L Q, I), M[s, s] = I,
+  M[s[:r], others] = Q1^T M^, and the Q2 rows are decoupled (set to zero).
+* Merge: a parent's slots are its children's surviving slots.
+
+This is a second, independent implementation written against the same
+equations; it shares no code with `sgf` beyond the partition and the basis
+evaluation.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .basis import Basis
+from .sgf import Options, _eligible, dof_list, point_coords
+
+
+def _cell_dofs(H, box):
+    nx, ny, nz = H.n
+    xs = np.arange(box[0][0], box[1][0] + 1)
+    ys = np.arange(box[0][1], box[1][1] + 1)
+    zs = np.arange(box[0][2], box[1][2] + 1)
+    zz, yy, xx = np.meshgrid(zs, ys, xs, indexing="ij")
+    pts = (xx + nx * (yy + ny * zz)).ravel()
+    return np.sort(pts)
+
+
+def dense_sgf(A, H, opts: Options = Options()):
+    """Return (A_l, [A_1, ..., A_l], ranks) built with explicit dense factors."""
+    A = A.toarray() if hasattr(A, "toarray") else np.asarray(A)
+    n = A.shape[0]
+    basis = Basis(H.dim, opts.degree, opts.basis, H.dof)
+    xyz = point_coords(H)
+    M = A.copy()
+    F = np.eye(n)
+    lev1 = H.levels[0]
+    slots = {i: list(dof_list(p, H.dof)) for i, p in enumerate(lev1.points)}
+    approx = []
+    ranks = {}
+
+    def Pi_of(lev, X):
+        pts = _cell_dofs(H, lev.box[X])
+        P = np.zeros((n, basis.pi))
+        P[dof_list(pts, H.dof)] = basis.evaluate(xyz[pts], lev.box[X])
+        return P
+
+    for li, lev in enumerate(H.levels):
+        if lev.top:
+            approx.append(F @ M @ F.T)
+            break
+        for I in lev.interiors():
+            s = slots[I]
+            if not s:
+                continue
+            rest = [q for X in slots if X != I for q in slots[X]]
+            L = sla.cholesky(M[np.ix_(s, s)], lower=True)
+            W = sla.solve_triangular(L, M[np.ix_(s, rest)], lower=True)
+            G_cols = np.zeros((n, len(s)))
+            G_cols[s] = L
+            G_cols[rest] = W.T
+            F[:, s] = F @ G_cols
+            M[np.ix_(rest, rest)] -= W.T @ W
+            M[np.ix_(s, s)] = np.eye(len(s))
+            M[np.ix_(s, rest)] = 0.0
+            M[np.ix_(rest, s)] = 0.0
+            del slots[I]
+        for B in [X for X in lev.separators() if _eligible(lev, X, H.dim, opts)]:
+            s = slots[B]
+            others_nodes = [X for X in slots if X != B]
+            others = [q for X in others_nodes for q in slots[X]]
+            L = sla.cholesky(M[np.ix_(s, s)], lower=True)
+            Mh = sla.solve_triangular(L, M[np.ix_(s, others)], lower=True)
+            FT = F.T
+            cols = [L.T @ (FT @ Pi_of(lev, B))[s]]
+            o = 0
+            for X in others_nodes:
+                k = len(slots[X])
+                cols.append(Mh[:, o:o + k] @ (FT @ Pi_of(lev, X))[slots[X]])
+                o += k
+            Nmat = np.hstack(cols)
+            Q, R, _ = sla.qr(Nmat, pivoting=True)
+            d = np.abs(np.diag(R))
+            r = int(np.sum(d > opts.tau * d[0]))
+            m = len(s)
+            ranks[(lev.t, B)] = (m, r, r < m)
+            if r < m:
+                F[:, s] = F[:, s] @ (L @ Q)
+                Mp = Q.T @ Mh
+                M[np.ix_(s, s)] = np.eye(m)
+                M[np.ix_(s[:r], others)] = Mp[:r]
+                M[np.ix_(others, s[:r])] = Mp[:r].T
+                M[np.ix_(s[r:], others)] = 0.0
+                M[np.ix_(others, s[r:])] = 0.0
+                slots[B] = s[:r]
+        approx.append(F @ M @ F.T)
+        nxt = H.levels[li + 1]
+        slots = {D: [q for C in kids for q in slots[C]] for D, kids in enumerate(nxt.children)}
+    return approx[-1], approx, ranks

@@ -1,0 +1,215 @@
+"""Pins for the SGF oracle (Algorithm 4.1) against what the paper fixes.
+
+P1  compression off => exact block Cholesky (Sec. 2.1: without compression the
+    factorization is an exact block Cholesky decomposition).
+P2  A_l Pi = A Pi (Eq. (preserve-pi), Prop. 6.1) and, per level,
+    E_i Pi_B = 0 for B in P_k, i <= k.
+P3  Q2^T N = 0 up to the rank tolerance (Eq. (QR)).
+P4  SPD: positive pivots, positive spectrum of A_l (Lemma 3.1).
+P5  explicit dense G_i, B_i restatement reproduces A_l (Sec. 2.1, Eq. (M')).
+P6  compressions inside a level commute (random order == canonical order).
+P7  trends: near-flat CG counts in n; higher degree => fewer iterations;
+    E_n = ||(A - A_l) v_n|| / lambda_n stays O(1) (Table 5.1).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import sgf_inputs as si
+from oracle.assemble import assemble, assemble_scalar
+from oracle.basis import eval_monomials, exponents
+from oracle.dense import dense_sgf
+from oracle.partition import build_hierarchy
+from oracle.pcg import pcg
+from oracle.sgf import Options, factorize, dof_list
+
+
+def _grid_problem(n, dim, b, stencil, seed=0, weight=1.0, dmask=None):
+    rng = np.random.default_rng(seed)
+    shape = (n[1], n[0]) if dim == 2 else (n[2], n[1], n[0])
+    k = np.exp(rng.standard_normal(shape))
+    if dmask is None:
+        dmask = 15 if dim == 2 else 1
+    A = assemble_scalar(n, dim, k, dmask, weight)
+    H = build_hierarchy(n, dim, b, stencil)
+    return A, H
+
+
+def _global_poly(H, degree):
+    nx, ny, nz = H.n
+    p = np.arange(nx * ny * nz)
+    xyz = np.stack([p % nx, (p // nx) % ny, p // (nx * ny)], 1).astype(float)
+    return eval_monomials(xyz, exponents(H.dim, degree))
+
+
+def _elimination_order(F):
+    """DOF ids in elimination order when nothing is compressed."""
+    H = F.H
+    vars_ = {i: list(v) for i, v in enumerate(F.vars1)}
+    order = []
+    for li, lev in enumerate(H.levels):
+        if lev.top:
+            order += vars_[0]
+            break
+        for I in lev.interiors():
+            order += vars_[I]
+        nxt = H.levels[li + 1]
+        vars_ = {D: [q for C in kids for q in vars_[C]] for D, kids in enumerate(nxt.children)}
+    return np.array(order)
+
+
+@pytest.mark.parametrize("n,dim,b,st", [((29, 23, 1), 2, 4, "5pt_2d"), ((13, 11, 9), 3, 4, "7pt_fv_3d")])
+def test_P1_no_compression_is_exact_block_cholesky(n, dim, b, st):
+    A, H = _grid_problem(n, dim, b, st, weight=2.0 if dim == 3 else 1.0)
+    F = factorize(A, H, Options(scheme="none", degree=1))
+    perm = _elimination_order(F)
+    assert np.array_equal(np.sort(perm), np.arange(A.shape[0]))
+    Lfull = sla.cholesky(A.toarray()[np.ix_(perm, perm)], lower=True)
+    pos = np.empty_like(perm)
+    pos[perm] = np.arange(perm.size)
+    # rebuild the DOF lists of every node to locate each factor block in Lfull
+    vars_ = {i: list(v) for i, v in enumerate(F.vars1)}
+    lev_i = 0
+    scale = np.abs(Lfull).max()
+    for op in F.ops:
+        if op[0] == "elim":
+            _, t, I, L, S_list, W = op
+            pi = pos[vars_[I]]
+            assert np.abs(Lfull[np.ix_(pi, pi)] - L).max() <= 1e-13 * scale
+            for S, Ws in zip(S_list, W):
+                ps = pos[vars_[S]]
+                assert np.abs(Lfull[np.ix_(ps, pi)] - Ws.T).max() <= 1e-13 * scale
+        elif op[0] == "merge":
+            vars_ = {D: [q for C in kids for q in vars_[C]] for D, kids, _ in op[2]}
+        elif op[0] == "top":
+            pt = pos[vars_[0]]
+            assert np.abs(Lfull[np.ix_(pt, pt)] - op[1]).max() <= 1e-13 * scale
+    rng = np.random.default_rng(1)
+    b_ = rng.standard_normal(A.shape[0])
+    assert np.linalg.norm(F.solve(b_) - sla.solve(A.toarray(), b_)) <= 1e-12 * np.linalg.norm(sla.solve(A.toarray(), b_))
+    x, it, res = pcg(lambda v: A @ v, F.solve, b_)
+    assert it == 1 and res < 1e-12
+
+
+@pytest.mark.parametrize("name,deg", [("poisson2d_64", 1), ("grf3d_24", 2), ("twophase3d_24", 2)])
+def test_P2_preserves_action_on_polynomials(name, deg):
+    cfg = si.config(name)
+    A = assemble(cfg)
+    H = build_hierarchy(cfg["n"], cfg["dim"], cfg["leaf"], cfg["stencil"])
+    F = factorize(A, H, Options(degree=deg))
+    assert any(v[2] for v in F.ranks().values()), "some node must actually compress"
+    Pi = _global_poly(H, deg)
+    AP = A @ Pi
+    err = np.linalg.norm(np.stack([F.multiply(Pi[:, k]) for k in range(Pi.shape[1])], 1) - AP)
+    assert err <= 1e-12 * np.linalg.norm(AP)
+
+
+def test_P2_per_level_error_annihilates_level_polynomials():
+    A, H = _grid_problem((23, 21, 1), 2, 4, "5pt_2d", seed=4)
+    opts = Options(degree=0)
+    Al, approx, ranks = dense_sgf(A, H, opts)
+    assert any(v[2] for v in ranks.values())
+    Ad = A.toarray()
+    prev = Ad
+    errs = []
+    for k, Ak in enumerate(approx):
+        errs.append(Ak - prev)
+        prev = Ak
+    Pi = _global_poly(H, 0)
+    nx = H.n[0]
+    for k, lev in enumerate(H.levels[:-1]):
+        for B in range(lev.nnodes):
+            lo, hi = lev.box[B]
+            p = np.arange(Ad.shape[0])
+            inside = (p % nx >= lo[0]) & (p % nx <= hi[0]) & (p // nx >= lo[1]) & (p // nx <= hi[1])
+            PiB = Pi * inside[:, None]
+            for i in range(k + 1):
+                assert np.abs(errs[i] @ PiB).max() <= 1e-11 * np.abs(Ad).max() * np.abs(Pi).max()
+
+
+def test_P3_Q2_annihilates_filtered_interaction_matrix():
+    cfg = si.config("grf3d_24")
+    A = assemble(cfg)
+    H = build_hierarchy(cfg["n"], 3, 8, cfg["stencil"])
+    F = factorize(A, H, Options(degree=2))
+    for info in F.comp_info.values():
+        assert info["q2n"] <= 10 * 1e-12 * info["nnorm"]
+
+
+def test_P4_spd_pivots_and_spectrum():
+    A, H = _grid_problem((19, 17, 1), 2, 4, "5pt_2d", seed=2)
+    F = factorize(A, H, Options(degree=1))
+    assert F.pivots_min > 0
+    Al = F.dense_operator()
+    assert np.abs(Al - Al.T).max() <= 1e-12 * np.abs(Al).max()
+    assert np.linalg.eigvalsh(0.5 * (Al + Al.T))[0] > 0
+
+
+@pytest.mark.parametrize("n,seed,deg", [((15, 15, 1), 0, 0), ((17, 13, 1), 3, 1), ((19, 17, 1), 0, 2)])
+def test_P5_dense_brute_force_reproduces_block_oracle(n, seed, deg):
+    A, H = _grid_problem(n, 2, 4, "5pt_2d", seed=seed)
+    F = factorize(A, H, Options(degree=deg))
+    Ad, _, ranks = dense_sgf(A, H, Options(degree=deg))
+    assert ranks == F.ranks()
+    assert any(v[2] for v in ranks.values())
+    Al = F.dense_operator()
+    assert np.abs(Al - Ad).max() <= 1e-12 * np.abs(Ad).max()
+    Ainv = F.dense_inverse()
+    assert np.abs(Ainv @ Ad - np.eye(Ad.shape[0])).max() <= 1e-10
+
+
+def test_P6_compression_order_inside_a_level_does_not_matter():
+    cfg = si.config("grf3d_24")
+    A = assemble(cfg)
+    H = build_hierarchy(cfg["n"], 3, 8, cfg["stencil"])
+    F1 = factorize(A, H, Options(degree=2))
+    F2 = factorize(A, H, Options(degree=2), order_seed=7)
+    assert F1.ranks() == F2.ranks()
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        v = rng.standard_normal(A.shape[0])
+        a, b = F1.solve(v), F2.solve(v)
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+        a, b = F1.multiply(v), F2.multiply(v)
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_P7_iteration_trends_and_smooth_eigenvector_accuracy():
+    its = {}
+    for e in (16, 32):
+        cfg = si.config(f"poisson3d_{e}")
+        A = assemble(cfg)
+        H = build_hierarchy(cfg["n"], 3, 8, cfg["stencil"])
+        for deg in (0, 2):
+            F = factorize(A, H, Options(degree=deg))
+            _, it, res = pcg(lambda v: A @ v, F.solve, si.rhs(A.shape[0], 0))
+            assert res <= 1e-10
+            its[(e, deg)] = it
+            if deg == 2:
+                x = np.arange(1, e + 1)
+                s = np.sin(np.pi * x / (e + 1))
+                vn = np.einsum("i,j,k->ijk", s, s, s).ravel()
+                vn /= np.linalg.norm(vn)
+                lam = 3 * (2 - 2 * np.cos(np.pi / (e + 1)))
+                En = np.linalg.norm(A @ vn - F.multiply(vn)) / lam
+                assert En < 2.0          # Table 5.1 reports O(1) values for pcw. quad.
+    assert its[(32, 2)] <= its[(16, 2)] + 8
+    assert its[(16, 2)] < its[(16, 0)] and its[(32, 2)] < its[(32, 0)]
+
+
+def test_pcg_finite_termination_and_exact_preconditioner():
+    # CG on an SPD matrix with k distinct eigenvalues ends in k steps (exactly,
+    # up to rounding); with the exact inverse as preconditioner it ends in one.
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    ev = np.repeat([1.0, 3.0, 7.0, 20.0], 10)
+    A = Q @ np.diag(ev) @ Q.T
+    b = rng.standard_normal(40)
+    _, it, res = pcg(lambda v: A @ v, lambda v: v, b, rtol=1e-10)
+    assert it == 4 and res < 1e-10
+    Ainv = np.linalg.inv(A)
+    _, it, res = pcg(lambda v: A @ v, lambda v: Ainv @ v, b, rtol=1e-10)
+    assert it == 1
+    x1, it1, _ = pcg(lambda v: A @ v, lambda v: v / ev.mean(), b, flexible=True)
+    x2, it2, _ = pcg(lambda v: A @ v, lambda v: v / ev.mean(), b, flexible=False)
+    assert it1 == it2 and np.allclose(x1, x2, rtol=1e-8)
