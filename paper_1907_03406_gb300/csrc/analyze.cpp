@@ -1,0 +1,462 @@
+// Symbolic analysis for the SGF factorization (host C++).
+//
+// Partitions (Sec. 5.1): at level t the cut spacing is d = b * 2^(t-1); along
+// an axis with N unknowns the separator layers sit at the coordinates i with
+// (i+1) % d == 0 and i <= N-2, dropping the last one when fewer than d/2
+// unknowns follow it.  A node is the set of unknowns sharing, on every axis,
+// the same separator coordinate or the same interval between separators
+// (Defs. 2.1-2.4).  Cells spanning intervals on every axis are the interiors
+// eliminated by block Cholesky (Sec. 4.1); the others are separators, which
+// Nest-All-All compresses when their cell dimension is >= 1 and Nest-2-All
+// when it is dim-1 (Sec. 5.1).  The top level is the first without any
+// separator.
+//
+// Block sparsity: level-1 blocks follow the stencil couplings; eliminating an
+// interior couples all its separator neighbours pairwise (fill); compression
+// keeps the block pattern; a level-(t+1) pair exists when two of its nodes'
+// children were coupled after elimination at level t (Sec. 4.3).
+//
+// Node bases (Sec. 3.1): monomials of degree <= j of the local coordinates
+// u = (x - c) / h of each node's cell box (u = 0 on flat axes), and the exact
+// affine re-expansion matrices that express a parent's local monomials in a
+// child's (Sec. 4.4 merge).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <numeric>
+#include <unordered_set>
+
+#include "sgf_internal.h"
+
+namespace sgf {
+
+namespace {
+
+std::vector<int> axis_separators(int N, int d) {
+  std::vector<int> s;
+  for (int i = 0; i <= N - 2; ++i)
+    if ((i + 1) % d == 0) s.push_back(i);
+  if (!s.empty() && (double)(N - 1 - s.back()) < d / 2.0) s.pop_back();
+  return s;
+}
+
+// code of every coordinate: 2k inside interval k, 2k+1 on separator k
+std::vector<int> axis_codes(int N, const std::vector<int>& seps) {
+  std::vector<int> c(N);
+  size_t k = 0;
+  for (int i = 0; i < N; ++i) {
+    if (k < seps.size() && seps[k] == i) {
+      c[i] = 2 * (int)k + 1;
+      ++k;
+    } else {
+      c[i] = 2 * (int)k;
+    }
+  }
+  return c;
+}
+
+void code_extent(int N, const std::vector<int>& seps, int code, int& lo, int& hi) {
+  int k = code / 2;
+  if (code & 1) {
+    lo = hi = seps[k];
+    return;
+  }
+  lo = k > 0 ? seps[k - 1] + 1 : 0;
+  hi = k < (int)seps.size() ? seps[k] - 1 : N - 1;
+}
+
+struct Offset { int dx, dy, dz; };
+
+std::vector<Offset> positive_offsets(int stencil) {
+  // one direction of every symmetric coupling
+  if (stencil == SGF_STENCIL_5PT_2D) return {{1, 0, 0}, {0, 1, 0}};
+  if (stencil == SGF_STENCIL_7PT_3D || stencil == SGF_STENCIL_7PT_FV_3D)
+    return {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  std::vector<Offset> o;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int key = dx + 3 * dy + 9 * dz;
+        if (key > 0) o.push_back({dx, dy, dz});
+      }
+  return o;
+}
+
+// monomial exponents of Pi^j in the column order of Sec. 3.1
+std::vector<std::array<int, 3>> exponents(int dim, int degree) {
+  std::vector<std::array<int, 3>> e = {{0, 0, 0}};
+  if (dim == 3) {
+    if (degree >= 1) { e.push_back({1, 0, 0}); e.push_back({0, 1, 0}); e.push_back({0, 0, 1}); }
+    if (degree >= 2) {
+      e.push_back({2, 0, 0}); e.push_back({0, 2, 0}); e.push_back({0, 0, 2});
+      e.push_back({1, 1, 0}); e.push_back({0, 1, 1}); e.push_back({1, 0, 1});
+    }
+  } else {
+    if (degree >= 1) { e.push_back({1, 0, 0}); e.push_back({0, 1, 0}); }
+    if (degree >= 2) { e.push_back({2, 0, 0}); e.push_back({0, 2, 0}); e.push_back({1, 1, 0}); }
+  }
+  return e;
+}
+
+void frame_of(const int* box, double c[3], double h[3]) {
+  for (int a = 0; a < 3; ++a) {
+    c[a] = 0.5 * ((double)box[a] + (double)box[3 + a]);
+    h[a] = 0.5 * ((double)box[3 + a] - (double)box[a]);
+  }
+}
+
+double ipow(double x, int e) { return e == 0 ? 1.0 : (e == 1 ? x : x * x); }
+
+// R (pi x pi, col-major) with Pi_parent(p) = Pi_child(p) R on the child's points
+void reexpansion(const int* cbox, const int* pbox, const std::vector<std::array<int, 3>>& ex,
+                 double* R) {
+  double cc[3], hc[3], cp[3], hp[3], a[3], b[3];
+  frame_of(cbox, cc, hc);
+  frame_of(pbox, cp, hp);
+  for (int ax = 0; ax < 3; ++ax) {
+    a[ax] = hp[ax] > 0 ? hc[ax] / hp[ax] : 0.0;
+    b[ax] = hp[ax] > 0 ? (cc[ax] - cp[ax]) / hp[ax] : 0.0;
+  }
+  const int pi = (int)ex.size();
+  std::fill(R, R + pi * pi, 0.0);
+  std::map<std::array<int, 3>, int> col;
+  for (int i = 0; i < pi; ++i) col[ex[i]] = i;
+  static const double binom[3][3] = {{1, 0, 0}, {1, 1, 0}, {1, 2, 1}};
+  for (int j = 0; j < pi; ++j) {
+    const auto& e = ex[j];
+    // (a_x u + b_x)^ex (a_y v + b_y)^ey (a_z w + b_z)^ez, expanded
+    for (int kx = 0; kx <= e[0]; ++kx)
+      for (int ky = 0; ky <= e[1]; ++ky)
+        for (int kz = 0; kz <= e[2]; ++kz) {
+          double v = binom[e[0]][kx] * ipow(a[0], kx) * ipow(b[0], e[0] - kx) *
+                     binom[e[1]][ky] * ipow(a[1], ky) * ipow(b[1], e[1] - ky) *
+                     binom[e[2]][kz] * ipow(a[2], kz) * ipow(b[2], e[2] - kz);
+          R[col[{kx, ky, kz}] + (size_t)pi * j] += v;
+        }
+  }
+}
+
+}  // namespace
+
+int LevelLayout::col_of(int u, int v) const {
+  auto b = up_nb.begin() + up_ptr[u], e = up_nb.begin() + up_ptr[u + 1];
+  auto it = std::lower_bound(b, e, v);
+  if (it == e || *it != v) return -1;
+  return up_col[it - up_nb.begin()];
+}
+
+void build_layout(const LevelSym& L, const std::vector<int>& m, LevelLayout& o) {
+  const int nn = L.nnodes;
+  o.m = m;
+  o.dg_off.assign(nn, 0);
+  o.vec_off.assign(nn, 0);
+  int64_t off = 0, voff = 0;
+  for (int i = 0; i < nn; ++i) {
+    o.dg_off[i] = off;
+    off += (int64_t)m[i] * m[i];
+    o.vec_off[i] = voff;
+    voff += m[i];
+  }
+  o.dg_size = off;
+  o.vec_size = voff;
+  // upper neighbours: interiors from the pre-elimination pattern, separators
+  // from the post-elimination pattern
+  std::vector<std::vector<int>> up(nn);
+  for (size_t p = 0; p < L.pairs.size(); p += 2) {
+    int u = L.pairs[p], v = L.pairs[p + 1];
+    if (L.interior[u]) up[u].push_back(v);
+  }
+  for (size_t p = 0; p < L.post.size(); p += 2) up[L.post[p]].push_back(L.post[p + 1]);
+  o.up_ptr.assign(nn + 1, 0);
+  o.up_nb.clear();
+  o.up_col.clear();
+  o.up_off.assign(nn, 0);
+  o.up_w.assign(nn, 0);
+  off = 0;
+  for (int u = 0; u < nn; ++u) {
+    auto& v = up[u];
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    o.up_off[u] = off;
+    int col = 0;
+    for (int w : v) {
+      o.up_nb.push_back(w);
+      o.up_col.push_back(col);
+      col += m[w];
+    }
+    o.up_w[u] = col;
+    o.up_ptr[u + 1] = (int)o.up_nb.size();
+    off += (int64_t)m[u] * col;
+  }
+  o.up_size = off;
+}
+
+int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::string& err) {
+  if (!g || !op) { err = "null argument"; return SGF_ERR_INVALID_ARG; }
+  if (stencil == SGF_STENCIL_Q1_ELASTIC_3D) {
+    err = "Q1 elasticity is not implemented in this build";
+    return SGF_ERR_UNSUPPORTED;
+  }
+  if (stencil < 0 || stencil > SGF_STENCIL_Q1_ELASTIC_3D) { err = "bad stencil"; return SGF_ERR_INVALID_ARG; }
+  const int dim = g->dim;
+  if (dim != 2 && dim != 3) { err = "dim must be 2 or 3"; return SGF_ERR_INVALID_ARG; }
+  if ((stencil == SGF_STENCIL_5PT_2D) != (dim == 2)) { err = "stencil/dim mismatch"; return SGF_ERR_INVALID_ARG; }
+  if (g->dof != 1) { err = "only scalar problems (dof = 1) in this build"; return SGF_ERR_UNSUPPORTED; }
+  for (int a = 0; a < dim; ++a)
+    if (g->n[a] < 1 || g->n[a] > (1 << 14)) { err = "grid size out of range"; return SGF_ERR_INVALID_ARG; }
+  if (op->leaf < 2) { err = "leaf must be >= 2"; return SGF_ERR_INVALID_ARG; }
+  if (op->degree < 0 || op->degree > 2) { err = "degree must be 0, 1 or 2"; return SGF_ERR_INVALID_ARG; }
+  if (op->basis != SGF_BASIS_POLY) { err = "only the polynomial basis for scalar problems"; return SGF_ERR_UNSUPPORTED; }
+  if (op->scheme < 0 || op->scheme > 2) { err = "bad scheme"; return SGF_ERR_INVALID_ARG; }
+  if (op->precision != SGF_PREC_FP64 && op->precision != SGF_PREC_MIXED) { err = "bad precision"; return SGF_ERR_INVALID_ARG; }
+
+  P.grid = *g;
+  P.stencil = stencil;
+  P.opts = *op;
+  P.nx = g->n[0];
+  P.ny = g->n[1];
+  P.nz = dim == 3 ? g->n[2] : 1;
+  P.npts = (int64_t)P.nx * P.ny * P.nz;
+  if (P.npts > (int64_t)1 << 30) { err = "grid too large"; return SGF_ERR_INVALID_ARG; }
+  P.dof = g->dof;
+  P.n = P.npts * P.dof;
+  const auto ex = exponents(dim, op->degree);
+  P.pi = (int)ex.size();
+  P.tau = op->tau > 0 ? op->tau : (op->precision == SGF_PREC_MIXED ? 1e-6 : 1e-12);
+  const int N[3] = {P.nx, P.ny, P.nz};
+
+  std::vector<int> prev_node_of_point;  // level-t node of every point
+  int t = 1;
+  while (true) {
+    LevelSym L;
+    L.t = t;
+    const int64_t dd = (int64_t)op->leaf << (t - 1);
+    L.d = dd > (1 << 30) ? (1 << 30) : (int)dd;
+    std::vector<int> seps[3];
+    bool any = false;
+    for (int a = 0; a < 3; ++a) {
+      if (N[a] > 1) seps[a] = axis_separators(N[a], L.d);
+      any = any || !seps[a].empty();
+    }
+    if (!any) {
+      L.top = true;
+      L.nnodes = 1;
+      L.code = {0, 0, 0};
+      L.interior = {0};
+      L.cell_dim = {dim};
+      L.box = {0, 0, 0, P.nx - 1, P.ny - 1, P.nz - 1};
+      L.eligible = {0};
+      if (P.lev.empty()) {
+        L.pt_ptr = {0, (int)P.npts};
+        L.pt_idx.resize(P.npts);
+        std::iota(L.pt_idx.begin(), L.pt_idx.end(), 0);
+      } else {
+        const LevelSym& pv = P.lev.back();
+        L.child_ptr = {0};
+        for (int c = 0; c < pv.nnodes; ++c)
+          if (!pv.interior[c]) L.child_idx.push_back(c);
+        L.child_ptr.push_back((int)L.child_idx.size());
+      }
+      P.lev.push_back(std::move(L));
+      break;
+    }
+    std::vector<int> cx = axis_codes(P.nx, seps[0]), cy = axis_codes(P.ny, seps[1]),
+                     cz = axis_codes(P.nz, seps[2]);
+    const int KX = 2 * (int)seps[0].size() + 1, KY = 2 * (int)seps[1].size() + 1,
+              KZ = 2 * (int)seps[2].size() + 1;
+    // enumerate cells, sort interiors first then by (z, y, x) code
+    struct Cell { int z, y, x; bool in; };
+    std::vector<Cell> cells;
+    cells.reserve((size_t)KX * KY * KZ);
+    for (int z = 0; z < KZ; ++z)
+      for (int y = 0; y < KY; ++y)
+        for (int x = 0; x < KX; ++x)
+          cells.push_back({z, y, x, (x % 2 == 0) && (y % 2 == 0) && (z % 2 == 0)});
+    std::stable_sort(cells.begin(), cells.end(), [](const Cell& a, const Cell& b) {
+      if (a.in != b.in) return a.in;
+      if (a.z != b.z) return a.z < b.z;
+      if (a.y != b.y) return a.y < b.y;
+      return a.x < b.x;
+    });
+    L.nnodes = (int)cells.size();
+    std::vector<int> table((size_t)KX * KY * KZ);
+    L.code.resize(3 * L.nnodes);
+    L.interior.resize(L.nnodes);
+    L.cell_dim.resize(L.nnodes);
+    L.box.resize(6 * L.nnodes);
+    L.eligible.resize(L.nnodes);
+    for (int i = 0; i < L.nnodes; ++i) {
+      const Cell& c = cells[i];
+      table[((size_t)c.z * KY + c.y) * KX + c.x] = i;
+      L.code[3 * i] = c.z;
+      L.code[3 * i + 1] = c.y;
+      L.code[3 * i + 2] = c.x;
+      L.interior[i] = c.in;
+      int cd = (c.x % 2 == 0) + (c.y % 2 == 0) + (dim == 3 ? (c.z % 2 == 0) : 0);
+      L.cell_dim[i] = cd;
+      const int cc[3] = {c.x, c.y, c.z};
+      for (int a = 0; a < 3; ++a) code_extent(N[a], seps[a], cc[a], L.box[6 * i + a], L.box[6 * i + 3 + a]);
+      bool el = false;
+      if (!c.in && t >= std::max(1, op->compress_from_level)) {
+        if (op->scheme == SGF_SCHEME_NEST_ALL_ALL) el = cd >= 1;
+        else if (op->scheme == SGF_SCHEME_NEST_2_ALL) el = cd == dim - 1;
+      }
+      L.eligible[i] = el;
+    }
+    std::vector<int> node_of_point(P.npts);
+    for (int64_t p = 0; p < P.npts; ++p) {
+      int x = (int)(p % P.nx), y = (int)((p / P.nx) % P.ny), z = (int)(p / ((int64_t)P.nx * P.ny));
+      node_of_point[p] = table[((size_t)cz[z] * KY + cy[y]) * KX + cx[x]];
+    }
+    if (P.lev.empty()) {
+      L.pt_ptr.assign(L.nnodes + 1, 0);
+      for (int64_t p = 0; p < P.npts; ++p) L.pt_ptr[node_of_point[p] + 1]++;
+      for (int i = 0; i < L.nnodes; ++i) L.pt_ptr[i + 1] += L.pt_ptr[i];
+      L.pt_idx.resize(P.npts);
+      std::vector<int> fill(L.pt_ptr.begin(), L.pt_ptr.end() - 1);
+      for (int64_t p = 0; p < P.npts; ++p) L.pt_idx[fill[node_of_point[p]]++] = (int)p;
+    } else {
+      const LevelSym& pv = P.lev.back();
+      std::vector<std::vector<int>> kids(L.nnodes);
+      for (int c = 0; c < pv.nnodes; ++c) {
+        if (pv.interior[c]) continue;
+        const int* b = &pv.box[6 * c];
+        int64_t p = b[0] + (int64_t)P.nx * (b[1] + (int64_t)P.ny * b[2]);
+        kids[node_of_point[p]].push_back(c);
+      }
+      L.child_ptr.assign(1, 0);
+      for (int i = 0; i < L.nnodes; ++i) {
+        for (int c : kids[i]) L.child_idx.push_back(c);
+        L.child_ptr.push_back((int)L.child_idx.size());
+      }
+    }
+    prev_node_of_point.swap(node_of_point);
+    P.lev.push_back(std::move(L));
+    ++t;
+    if (t > 40) { err = "too many levels"; return SGF_ERR_INVALID_ARG; }
+  }
+  // children of the top level need the same treatment (handled above)
+
+  // ---- block patterns -------------------------------------------------
+  auto finish_post = [&](LevelSym& L) {
+    std::vector<std::vector<int>> nb(L.nnodes);
+    for (size_t p = 0; p < L.pairs.size(); p += 2) {
+      nb[L.pairs[p]].push_back(L.pairs[p + 1]);
+      nb[L.pairs[p + 1]].push_back(L.pairs[p]);
+    }
+    std::vector<int64_t> keys;
+    for (size_t p = 0; p < L.pairs.size(); p += 2) {
+      int u = L.pairs[p], v = L.pairs[p + 1];
+      if (!L.interior[u] && !L.interior[v]) keys.push_back((int64_t)u * L.nnodes + v);
+    }
+    for (int I = 0; I < L.nnodes; ++I) {
+      if (!L.interior[I]) continue;
+      auto& s = nb[I];
+      std::sort(s.begin(), s.end());
+      for (size_t a = 0; a < s.size(); ++a)
+        for (size_t b = a + 1; b < s.size(); ++b) keys.push_back((int64_t)s[a] * L.nnodes + s[b]);
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    L.post.clear();
+    for (int64_t k : keys) {
+      L.post.push_back((int)(k / L.nnodes));
+      L.post.push_back((int)(k % L.nnodes));
+    }
+  };
+  if (!P.lev[0].top) {
+    LevelSym& L1 = P.lev[0];
+    std::vector<int> node_of(P.npts);
+    for (int i = 0; i < L1.nnodes; ++i)
+      for (int k = L1.pt_ptr[i]; k < L1.pt_ptr[i + 1]; ++k) node_of[L1.pt_idx[k]] = i;
+    std::vector<int64_t> keys;
+    for (auto o : positive_offsets(stencil)) {
+      for (int64_t p = 0; p < P.npts; ++p) {
+        int x = (int)(p % P.nx), y = (int)((p / P.nx) % P.ny), z = (int)(p / ((int64_t)P.nx * P.ny));
+        int qx = x + o.dx, qy = y + o.dy, qz = z + o.dz;
+        if (qx < 0 || qx >= P.nx || qy < 0 || qy >= P.ny || qz < 0 || qz >= P.nz) continue;
+        int u = node_of[p], v = node_of[qx + (int64_t)P.nx * (qy + (int64_t)P.ny * qz)];
+        if (u == v) continue;
+        keys.push_back((int64_t)std::min(u, v) * L1.nnodes + std::max(u, v));
+      }
+      std::sort(keys.begin(), keys.end());
+      keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    }
+    for (int64_t k : keys) {
+      L1.pairs.push_back((int)(k / L1.nnodes));
+      L1.pairs.push_back((int)(k % L1.nnodes));
+    }
+    finish_post(L1);
+    for (size_t li = 1; li < P.lev.size(); ++li) {
+      LevelSym& L = P.lev[li];
+      const LevelSym& pv = P.lev[li - 1];
+      if (L.top) break;
+      std::vector<int> parent(pv.nnodes, -1);
+      for (int D = 0; D < L.nnodes; ++D)
+        for (int k = L.child_ptr[D]; k < L.child_ptr[D + 1]; ++k) parent[L.child_idx[k]] = D;
+      std::vector<int64_t> pk;
+      for (size_t p = 0; p < pv.post.size(); p += 2) {
+        int a = parent[pv.post[p]], b = parent[pv.post[p + 1]];
+        if (a != b) pk.push_back((int64_t)std::min(a, b) * L.nnodes + std::max(a, b));
+      }
+      std::sort(pk.begin(), pk.end());
+      pk.erase(std::unique(pk.begin(), pk.end()), pk.end());
+      for (int64_t k : pk) {
+        L.pairs.push_back((int)(k / L.nnodes));
+        L.pairs.push_back((int)(k % L.nnodes));
+      }
+      finish_post(L);
+    }
+  }
+
+  // ---- bases and re-expansion (Sec. 3.1, Sec. 4.4) ---------------------
+  {
+    const LevelSym& L1 = P.lev[0];
+    P.phi1_off.assign(L1.nnodes + 1, 0);
+    for (int i = 0; i < L1.nnodes; ++i)
+      P.phi1_off[i + 1] = P.phi1_off[i] + (int64_t)(L1.pt_ptr[i + 1] - L1.pt_ptr[i]) * P.pi;
+    P.phi1.assign(P.phi1_off.back(), 0.0);
+    for (int i = 0; i < L1.nnodes; ++i) {
+      double c[3], h[3];
+      frame_of(&L1.box[6 * i], c, h);
+      const int m = L1.pt_ptr[i + 1] - L1.pt_ptr[i];
+      double* F = &P.phi1[P.phi1_off[i]];
+      for (int r = 0; r < m; ++r) {
+        int64_t p = L1.pt_idx[L1.pt_ptr[i] + r];
+        double xyz[3] = {(double)(p % P.nx), (double)((p / P.nx) % P.ny), (double)(p / ((int64_t)P.nx * P.ny))};
+        double u[3];
+        for (int a = 0; a < 3; ++a) u[a] = h[a] > 0 ? (xyz[a] - c[a]) / h[a] : 0.0;
+        for (int j = 0; j < P.pi; ++j)
+          F[r + (size_t)m * j] = ipow(u[0], ex[j][0]) * ipow(u[1], ex[j][1]) * ipow(u[2], ex[j][2]);
+      }
+    }
+    for (size_t li = 1; li < P.lev.size(); ++li) {
+      LevelSym& L = P.lev[li];
+      const LevelSym& pv = P.lev[li - 1];
+      L.reexp.assign(L.child_idx.size() * (size_t)P.pi * P.pi, 0.0);
+      for (int D = 0; D < L.nnodes; ++D)
+        for (int k = L.child_ptr[D]; k < L.child_ptr[D + 1]; ++k)
+          reexpansion(&pv.box[6 * L.child_idx[k]], &L.box[6 * D], ex, &L.reexp[(size_t)k * P.pi * P.pi]);
+    }
+  }
+
+  // ---- structural size bounds (no compression) -------------------------
+  P.mcap.resize(P.lev.size());
+  for (size_t li = 0; li < P.lev.size(); ++li) {
+    const LevelSym& L = P.lev[li];
+    P.mcap[li].assign(L.nnodes, 0);
+    for (int i = 0; i < L.nnodes; ++i) {
+      if (li == 0) {
+        P.mcap[li][i] = (L.pt_ptr[i + 1] - L.pt_ptr[i]) * P.dof;
+      } else {
+        int s = 0;
+        for (int k = L.child_ptr[i]; k < L.child_ptr[i + 1]; ++k) s += P.mcap[li - 1][L.child_idx[k]];
+        P.mcap[li][i] = s;
+      }
+    }
+  }
+  return SGF_OK;
+}
+
+}  // namespace sgf

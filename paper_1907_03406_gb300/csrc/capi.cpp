@@ -1,0 +1,271 @@
+// C ABI of the SGF library (declared in include/sgf.h).  Every entry point
+// converts internal exceptions into status codes; nothing throws across it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "devmem.h"
+#include "factor.h"
+#include "sgf.h"
+#include "sgf_internal.h"
+
+struct sgf_plan {
+  sgf::Plan p;
+};
+
+struct sgf_factor_s {
+  std::unique_ptr<sgf::FactorBase> f;
+  const sgf_plan* plan;
+};
+
+namespace {
+thread_local std::string g_last_error;
+
+template <class F>
+int guarded(F&& fn) {
+  try {
+    return fn();
+  } catch (const sgf::SgfError& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return SGF_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return SGF_ERR_CUDA;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+const char* sgf_status_string(int s) {
+  switch (s) {
+    case SGF_OK: return "ok";
+    case SGF_ERR_INVALID_ARG: return "invalid argument";
+    case SGF_ERR_NOT_SPD: return "matrix not SPD (non-positive pivot)";
+    case SGF_ERR_NONFINITE: return "non-finite value";
+    case SGF_ERR_OOM: return "out of memory";
+    case SGF_ERR_NO_CONVERGENCE: return "PCG did not converge";
+    case SGF_ERR_TIMEOUT: return "device wait timed out";
+    case SGF_ERR_CUDA: return "CUDA error";
+    case SGF_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+const char* sgf_last_error(void) { return g_last_error.c_str(); }
+
+int sgf_analyze(const sgf_grid* grid, int stencil, const sgf_opts* opts, sgf_plan** out) {
+  if (!out) return SGF_ERR_INVALID_ARG;
+  *out = nullptr;
+  return guarded([&] {
+    auto p = std::make_unique<sgf_plan>();
+    std::string err;
+    int rc = sgf::analyze(grid, stencil, opts, p->p, err);
+    if (rc != SGF_OK) {
+      g_last_error = err;
+      return rc;
+    }
+    *out = p.release();
+    return (int)SGF_OK;
+  });
+}
+
+void sgf_plan_destroy(sgf_plan* plan) { delete plan; }
+
+int sgf_plan_info(const sgf_plan* plan, int* nlevels, int64_t* n) {
+  if (!plan) return SGF_ERR_INVALID_ARG;
+  if (nlevels) *nlevels = (int)plan->p.lev.size();
+  if (n) *n = plan->p.n;
+  return SGF_OK;
+}
+
+int sgf_plan_export_level(const sgf_plan* plan, int level, int* nnodes, int* npairs, int* npost,
+                          int* codes, int* flags, int* child_ptr, int* child_idx, int* pairs,
+                          int* post) {
+  if (!plan || level < 0 || level >= (int)plan->p.lev.size()) return SGF_ERR_INVALID_ARG;
+  const sgf::LevelSym& L = plan->p.lev[level];
+  if (nnodes) *nnodes = L.nnodes;
+  if (npairs) *npairs = (int)L.pairs.size() / 2;
+  if (npost) *npost = (int)L.post.size() / 2;
+  if (codes) std::copy(L.code.begin(), L.code.end(), codes);
+  if (flags)
+    for (int i = 0; i < L.nnodes; ++i) flags[i] = (L.interior[i] ? 1 : 0) | (L.cell_dim[i] << 4) | (L.eligible[i] ? 2 : 0);
+  if (child_ptr) {
+    if (L.child_ptr.empty()) std::fill(child_ptr, child_ptr + L.nnodes + 1, 0);
+    else std::copy(L.child_ptr.begin(), L.child_ptr.end(), child_ptr);
+  }
+  if (child_idx) std::copy(L.child_idx.begin(), L.child_idx.end(), child_idx);
+  if (pairs) std::copy(L.pairs.begin(), L.pairs.end(), pairs);
+  if (post) std::copy(L.post.begin(), L.post.end(), post);
+  return SGF_OK;
+}
+
+int sgf_plan_footprint(const sgf_plan* plan, size_t* b64, size_t* bmx) {
+  if (!plan) return SGF_ERR_INVALID_ARG;
+  // structural bound: every node kept at its uncompressed size
+  const sgf::Plan& P = plan->p;
+  double words = 0;
+  for (size_t li = 0; li < P.lev.size(); ++li) {
+    sgf::LevelLayout lay;
+    sgf::build_layout(P.lev[li], P.mcap[li], lay);
+    words += 3.0 * lay.dg_size + 2.0 * lay.up_size + 3.0 * lay.vec_size + P.pi * lay.vec_size;
+  }
+  const double extra = 64.0 * P.npts;  // stencil arrays, maps, vectors
+  if (b64) *b64 = (size_t)(8.0 * words + extra);
+  if (bmx) *bmx = (size_t)(4.0 * words + extra);
+  return SGF_OK;
+}
+
+int sgf_factor(const sgf_plan* plan, const double* coeffs_dev, void* stream, sgf_factor_t** out) {
+  if (!out) return SGF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!plan || !coeffs_dev) return SGF_ERR_INVALID_ARG;
+  return guarded([&] {
+    auto f = std::make_unique<sgf_factor_s>();
+    f->plan = plan;
+    f->f = sgf::make_factor(plan->p, coeffs_dev, (cudaStream_t)stream);
+    *out = f.release();
+    return (int)SGF_OK;
+  });
+}
+
+void sgf_factor_destroy(sgf_factor_t* f) { delete f; }
+
+int sgf_factor_level_stats(const sgf_factor_t* f, int level, int* ncomp, int64_t* before,
+                           int64_t* after, int64_t* bytes) {
+  if (!f || level < 0 || level >= (int)f->f->stats.size()) return SGF_ERR_INVALID_ARG;
+  const auto& s = f->f->stats[level];
+  if (ncomp) *ncomp = s.ncomp;
+  if (before) *before = s.size_before;
+  if (after) *after = s.size_after;
+  if (bytes) *bytes = s.bytes;
+  return SGF_OK;
+}
+
+int sgf_factor_ranks(const sgf_factor_t* f, int level, int* m, int* r) {
+  if (!f || level < 0 || level >= (int)f->f->stats.size()) return SGF_ERR_INVALID_ARG;
+  const auto& s = f->f->stats[level];
+  if (m) std::copy(s.m.begin(), s.m.end(), m);
+  if (r) std::copy(s.r.begin(), s.r.end(), r);
+  return SGF_OK;
+}
+
+int sgf_factor_status(const sgf_factor_t* f, int* bl, int* bn) {
+  if (!f) return SGF_ERR_INVALID_ARG;
+  if (bl) *bl = f->f->bad_level;
+  if (bn) *bn = f->f->bad_node;
+  return f->f->status;
+}
+
+static int apply_common(const sgf_factor_t* f, const double* x, double* y, int nrhs, void* stream,
+                        int which) {
+  if (!f || !x || !y || nrhs < 1 || x == y) return SGF_ERR_INVALID_ARG;
+  return guarded([&] {
+    const int64_t n = f->f->n;
+    for (int j = 0; j < nrhs; ++j) {
+      if (which == 0) f->f->apply(x + j * n, y + j * n, (cudaStream_t)stream);
+      else if (which == 1) f->f->multiply(x + j * n, y + j * n, (cudaStream_t)stream);
+      else f->f->spmv(x + j * n, y + j * n, (cudaStream_t)stream);
+    }
+    if (!sgf::dry_run()) SGF_CK(cudaGetLastError());
+    return (int)SGF_OK;
+  });
+}
+
+int sgf_apply(const sgf_factor_t* f, const double* x, double* y, int nrhs, void* stream) {
+  return apply_common(f, x, y, nrhs, stream, 0);
+}
+int sgf_apply_forward(const sgf_factor_t* f, const double* x, double* y, int nrhs, void* stream) {
+  return apply_common(f, x, y, nrhs, stream, 1);
+}
+int sgf_spmv(const sgf_factor_t* f, const double* x, double* y, int nrhs, void* stream) {
+  return apply_common(f, x, y, nrhs, stream, 2);
+}
+
+int sgf_pcg_solve(const sgf_factor_t* f, const double* b, double* x, int nrhs, double rtol, int maxit,
+                  void* stream, sgf_solve_info* info) {
+  if (!f || !b || !x || nrhs < 1 || rtol <= 0 || maxit < 1 || b == x) return SGF_ERR_INVALID_ARG;
+  return guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    SGF_CK(cudaEventCreate(&e0));
+    SGF_CK(cudaEventCreate(&e1));
+    SGF_CK(cudaEventRecord(e0, s));
+    int worst = SGF_OK, itmax = 0;
+    double resmax = 0;
+    const int64_t n = f->f->n;
+    for (int j = 0; j < nrhs; ++j) {
+      int it = 0;
+      double rr = 0;
+      int rc = sgf::pcg_solve(*f->f, b + j * n, x + j * n, rtol, maxit, s, &it, &rr);
+      if (rc != SGF_OK) worst = rc;
+      itmax = std::max(itmax, it);
+      resmax = std::max(resmax, rr);
+    }
+    SGF_CK(cudaEventRecord(e1, s));
+    SGF_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+      info->iterations = itmax;
+      info->rel_residual = resmax;
+      info->seconds = ms * 1e-3;
+    }
+    return worst;
+  });
+}
+
+int sgf_solve_host(const sgf_plan* plan, const double* coeffs_host, const double* b_host,
+                   double* x_host, int nrhs, double rtol, int maxit, void* stream,
+                   sgf_solve_info* info) {
+  if (!plan || !coeffs_host || !b_host || !x_host || nrhs < 1) return SGF_ERR_INVALID_ARG;
+  return guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const sgf::Plan& P = plan->p;
+    const size_t nb = sizeof(double) * P.n * nrhs;
+    double *dc = nullptr, *db = nullptr, *dx = nullptr;
+    SGF_CK(cudaMallocAsync((void**)&dc, sizeof(double) * P.npts, s));
+    SGF_CK(cudaMallocAsync((void**)&db, nb, s));
+    SGF_CK(cudaMallocAsync((void**)&dx, nb, s));
+    SGF_CK(cudaMemcpyAsync(dc, coeffs_host, sizeof(double) * P.npts, cudaMemcpyHostToDevice, s));
+    SGF_CK(cudaMemcpyAsync(db, b_host, nb, cudaMemcpyHostToDevice, s));
+    sgf_factor_t* f = nullptr;
+    int rc = sgf_factor(plan, dc, stream, &f);
+    if (rc == SGF_OK) {
+      rc = sgf_pcg_solve(f, db, dx, nrhs, rtol, maxit, stream, info);
+      SGF_CK(cudaMemcpyAsync(x_host, dx, nb, cudaMemcpyDeviceToHost, s));
+      SGF_CK(cudaStreamSynchronize(s));
+      sgf_factor_destroy(f);
+    }
+    cudaFreeAsync(dc, s);
+    cudaFreeAsync(db, s);
+    cudaFreeAsync(dx, s);
+    SGF_CK(cudaStreamSynchronize(s));
+    return rc;
+  });
+}
+
+}  // extern "C"
+
+extern "C" {
+// Dry-run validation report (SGF_DRY_RUN=1): number of out-of-range task
+// accesses seen since the last reset, and a text log of the first ones.
+int64_t sgf_dry_run_violations(int reset) {
+  int64_t v = sgf::dry_run_violations();
+  if (reset) sgf::dry_run_reset();
+  return v;
+}
+const char* sgf_dry_run_report(void) {
+  thread_local std::string s;
+  s = sgf::dry_run_report();
+  return s.c_str();
+}
+}

@@ -1,0 +1,78 @@
+// Numeric factorization object behind the sgf_factor handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "sgf_internal.h"
+
+namespace sgf {
+
+struct SgfError : std::runtime_error {
+  int code;
+  SgfError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SGF_CK(x)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::sgf::SgfError(e_ == cudaErrorMemoryAllocation ? SGF_ERR_OOM : SGF_ERR_CUDA,  \
+                            std::string(#x) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+// Host staging of task arrays: pushed descriptors are uploaded with one copy,
+// then the recorded launches run against the device copy.
+struct Batch {
+  std::vector<char> host;
+  std::vector<char> keep_host;  // dry-run copy of a persistent program
+  std::vector<std::function<void(const char*)>> launches;
+  char* dev = nullptr;
+  size_t cap = 0;
+  template <class X>
+  size_t push(const std::vector<X>& v) {
+    size_t off = (host.size() + 63) & ~size_t(63);
+    host.resize(off + v.size() * sizeof(X));
+    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(X));
+    return off;
+  }
+  // upload and run everything recorded so far, then reset
+  void run(cudaStream_t s);
+  // keep the uploaded copy (for programs replayed many times)
+  void upload_persistent(cudaStream_t s);
+  void release(cudaStream_t s);
+};
+
+struct LevelStats {
+  int ncomp = 0;
+  int64_t size_before = 0, size_after = 0, bytes = 0;
+  std::vector<int> m, r;
+};
+
+class FactorBase {
+ public:
+  virtual ~FactorBase() = default;
+  virtual void apply(const double* x, double* y, cudaStream_t s) = 0;      // A_l^{-1}
+  virtual void multiply(const double* x, double* y, cudaStream_t s) = 0;   // A_l
+  virtual void spmv(const double* x, double* y, cudaStream_t s) = 0;       // A
+  virtual bool mixed() const = 0;
+  const Plan* plan = nullptr;
+  std::vector<LevelStats> stats;
+  int bad_level = -1, bad_node = -1, status = 0;
+  int64_t n = 0;
+};
+
+std::unique_ptr<FactorBase> make_factor(const Plan& plan, const double* coeffs_dev, cudaStream_t s);
+
+// PCG (Sec. 7) on an existing factor; returns SGF_OK or SGF_ERR_NO_CONVERGENCE
+int pcg_solve(FactorBase& F, const double* b, double* x, double rtol, int maxit, cudaStream_t s,
+              int* iters, double* relres);
+
+}  // namespace sgf

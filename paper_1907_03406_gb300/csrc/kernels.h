@@ -1,0 +1,64 @@
+// Launch wrappers of the SGF device kernels (implemented in kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sgf_internal.h"
+
+namespace sgf {
+
+// First device-side failure (pivot <= 0 / non-finite / size limits).
+struct DevStatus {
+  int code;   // 0 or an SGF_ERR_* value
+  int level;
+  int node;
+  int pad;
+};
+
+template <typename T>
+void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* contribs, int ntasks,
+                 cudaStream_t s);
+template <typename T>
+void launch_diag(const DiagTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
+template <typename S, typename D>
+void launch_copy(const CopyTask<S, D>* tasks, int ntasks, cudaStream_t s);
+template <typename T>
+void launch_qrcp(const QrTask<T>* tasks, int ntasks, int* ranks, double tau, int max_m, int max_c,
+                 DevStatus* st, int level, cudaStream_t s);
+template <typename T>
+void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks,
+                   cudaStream_t s);
+template <typename T>
+void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks,
+                   cudaStream_t s);
+template <typename T>
+void launch_veccopy(const VecCopyTask* tasks, int ntasks, const T* src, T* dst, cudaStream_t s);
+
+// Scalar stencil assembly (Sec. 7.1): FP64 SpMV diagonals and, through the
+// element map (stride 7 per point: x-, x+, y-, y+, z-, z+, diag; offsets into
+// the concatenation [Dg | Up], -1 = skip), the level-1 dense blocks.
+template <typename T>
+void launch_assemble_scalar(const double* coef, int nx, int ny, int nz, unsigned dirichlet,
+                            double bweight, const int64_t* map, int64_t dg_size, T* dg, T* up,
+                            double* sd, double* sx, double* sy, double* sz, cudaStream_t s);
+
+// y = A x for the assembled 5/7-point operator, FP64.
+void launch_spmv_stencil(const double* sd, const double* sx, const double* sy, const double* sz,
+                         int nx, int ny, int nz, const double* x, double* y, cudaStream_t s);
+
+// Deterministic dot product: partials (>= kDotBlocks doubles) then result[0].
+constexpr int kDotBlocks = 304;
+void launch_dot(const double* a, const double* b, int64_t n, double* partials, double* result,
+                cudaStream_t s);
+
+template <typename T>
+void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, cudaStream_t s);
+
+// y = a*x + y (FP64)
+void launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s);
+// p = z + b*p (FP64)
+void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s);
+
+}  // namespace sgf

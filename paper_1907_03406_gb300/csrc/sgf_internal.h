@@ -1,0 +1,155 @@
+// Internal data structures of the SGF library: the symbolic plan built by
+// sgf_analyze on the host, per-level block layouts, and the task descriptors
+// the batched device kernels consume.
+#pragma once
+
+#include <cstddef>
+#include <array>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sgf.h"
+
+namespace sgf {
+
+// ---------------------------------------------------------------------------
+// Symbolic plan (host)
+// ---------------------------------------------------------------------------
+
+// One level of the nested-dissection hierarchy (Sec. 5.1, Defs. 2.1-2.4).
+// Node order: interiors first, then separators, each sorted by the cell code
+// tuple (z, y, x); per axis code 2k = interval k, 2k+1 = separator k.
+struct LevelSym {
+  int t = 0;          // 1-based level
+  int d = 0;          // cut spacing b * 2^(t-1)
+  bool top = false;   // the single-node top level
+  int nnodes = 0;
+  std::vector<int> code;       // 3 per node: z, y, x
+  std::vector<char> interior;  // per node
+  std::vector<int> cell_dim;   // per node
+  std::vector<int> box;        // 6 per node: lo x,y,z then hi x,y,z
+  std::vector<char> eligible;  // per node: selected for compression
+  std::vector<int> child_ptr;  // nnodes + 1 (levels > 1)
+  std::vector<int> child_idx;  // previous-level node ids, canonical order
+  std::vector<int> pairs;      // pre-elimination block pairs (u < v), 2 ints each
+  std::vector<int> post;       // separator pairs after elimination (u < v)
+  std::vector<int> pt_ptr, pt_idx;  // level 1: natural point ids per node
+  std::vector<double> reexp;   // levels > 1: pi x pi (col-major) per child,
+                               // indexed like child_idx (Sec. 4.4 merge)
+};
+
+struct Plan {
+  sgf_grid grid{};
+  int stencil = 0;
+  sgf_opts opts{};
+  int nx = 1, ny = 1, nz = 1;
+  int64_t npts = 0, n = 0;
+  int dof = 1;
+  int pi = 1;                      // basis columns
+  double tau = 1e-12;
+  std::vector<LevelSym> lev;
+  // level-1 basis rows Phi (m x pi, col-major) per node, concatenated
+  std::vector<double> phi1;
+  std::vector<int64_t> phi1_off;
+  // structural upper bounds of node sizes per level (for the footprint)
+  std::vector<std::vector<int>> mcap;
+};
+
+// Per-level dense block layout for given node sizes.  Every node owns a full
+// m x m diagonal block and an "upper panel" holding its blocks with higher
+// numbered neighbours, side by side (column-major, leading dimension m):
+// interiors hold their separator blocks (pre-elimination pattern), separators
+// hold their separator blocks of the post-elimination pattern (fill included).
+struct LevelLayout {
+  std::vector<int> m;
+  std::vector<int64_t> dg_off;   // diagonal block offset (elements)
+  int64_t dg_size = 0;
+  std::vector<int> up_ptr;       // nnodes + 1 into up_nb / up_col
+  std::vector<int> up_nb;        // neighbour node ids (> owner), ascending
+  std::vector<int> up_col;       // column offset of each neighbour block
+  std::vector<int64_t> up_off;   // panel start (elements)
+  std::vector<int> up_w;         // panel width (columns)
+  int64_t up_size = 0;
+  std::vector<int64_t> vec_off;  // offset of each node in a level vector
+  int64_t vec_size = 0;
+
+  // column offset of block (u, v), u < v, inside u's panel; -1 if absent
+  int col_of(int u, int v) const;
+};
+
+void build_layout(const LevelSym& L, const std::vector<int>& m, LevelLayout& out);
+
+int analyze(const sgf_grid* g, int stencil, const sgf_opts* o, Plan& plan, std::string& err);
+
+// ---------------------------------------------------------------------------
+// Device task descriptors (one CTA per task unless stated)
+// ---------------------------------------------------------------------------
+constexpr int kTile = 64;
+
+template <typename T>
+struct GemmTask {        // C[M x N] = beta*C + alpha * sum_c op(A_c) op(B_c)
+  T* C;
+  int ldc, M, N;         // M, N <= kTile
+  int c_begin, c_count;  // contribution range
+  T alpha;
+  int beta;              // 0 or 1
+};
+
+enum : int { kTransA = 1, kTransB = 2 };
+
+template <typename T>
+struct GemmContrib {
+  const T* A;            // op(A) is M x K
+  const T* B;            // op(B) is K x N
+  int lda, ldb, K, flags;
+};
+
+enum : int { kCopy = 0, kCopyT = 1, kZero = 2, kIdentity = 3, kCopyLower = 4 };
+
+template <typename S, typename D>
+struct CopyTask {        // dst[rows x cols] <- mode(src), rows, cols <= kTile
+  const S* src;
+  D* dst;
+  int lds, ldd, rows, cols, mode, pad;
+};
+
+template <typename T>
+struct DiagTask {        // in-place Cholesky of an n x n tile (n <= kTile) and its inverse
+  T* A;                  // tile, ld = lda; gets L (strict upper part zeroed)
+  T* Li;                 // gets L^{-1}, ld = ldli
+  int lda, ldli, n, node;
+};
+
+template <typename T>
+struct QrTask {          // column-pivoted Householder QR of A (m x c, ld = m)
+  T* A;                  // in/out workspace
+  T* Q1;                 // out: m x r, ld = m (r = kept rank)
+  int m, c, node, pad;
+};
+
+template <typename T>
+struct GemvTask {        // y[M] = beta*y + sum_c alpha_c op(A_c) (x_c - x2_c)
+  T* y;
+  int M, c_begin, c_count, beta;
+};
+
+template <typename T>
+struct GemvContrib {
+  const T* A;            // column-major, ld = lda; op(A) is M x K
+  const T* x;            // K
+  const T* x2;           // K or nullptr (subtracted from x)
+  int lda, K;
+  int tri;               // 0: dense A; t > 0: A is (part of) a lower-triangular
+                         // matrix whose first row (op N) / column (op T) in this
+                         // chunk has absolute index t - 1: the zero half is skipped
+  T alpha;
+};
+
+struct VecCopyTask {     // dst[i] = src[i] for i < len (level-vector gathers)
+  int64_t src, dst;
+  int len, pad;
+};
+
+}  // namespace sgf

@@ -1,0 +1,200 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (the spec contract): FP64 apply of A_l^{-1} (and of A_l) on
+random vectors within 1e-10 relative of the oracle; ranks of every node
+equal; PCG iteration counts within +-1; true relative residual <= 1e-10.
+Mixed precision: PCG still reaches 1e-10 (FP64 outer loop) and the error of
+the FP32 apply against the FP64 oracle is reported and bounded by 1e-3.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import sgf_inputs as si
+from oracle.assemble import assemble, assemble_scalar
+from oracle.basis import eval_monomials, exponents
+from oracle.partition import build_hierarchy
+from oracle.pcg import pcg
+from oracle.sgf import Options, factorize
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1907_03406_gb300 as sgf  # noqa: E402
+
+DEV = torch.device("cuda:0")
+_ORACLE_CACHE = {}
+
+
+def _problem(name, seed=0):
+    if name.startswith("rand2d_"):
+        _, nx, ny, b = name.split("_")
+        nx, ny, b = int(nx), int(ny), int(b)
+        rng = np.random.default_rng(seed)
+        k = np.exp(rng.standard_normal((ny, nx)))
+        return dict(name=name, dim=2, n=(nx, ny, 1), stencil="5pt_2d", dirichlet=15, coeffs=k,
+                    leaf=b, degree=1, basis="poly", dof=1)
+    if name.startswith("rand3d_"):
+        _, nx, ny, nz, b = name.split("_")
+        nx, ny, nz, b = int(nx), int(ny), int(nz), int(b)
+        rng = np.random.default_rng(seed)
+        k = np.exp(1.5 * rng.standard_normal((nz, ny, nx)))
+        return dict(name=name, dim=3, n=(nx, ny, nz), stencil="7pt_fv_3d", dirichlet=1, coeffs=k,
+                    leaf=b, degree=2, basis="poly", dof=1)
+    return si.config(name, seed)
+
+
+def _oracle(cfg, scheme="nest_all_all"):
+    key = (cfg["name"], scheme)
+    if key not in _ORACLE_CACHE:
+        A = assemble(cfg)
+        H = build_hierarchy(cfg["n"], cfg["dim"], cfg["leaf"], cfg["stencil"])
+        F = factorize(A, H, Options(scheme=scheme, degree=cfg["degree"]))
+        _ORACLE_CACHE[key] = (A, H, F)
+    return _ORACLE_CACHE[key]
+
+
+def _gpu(cfg, precision="fp64", scheme="nest_all_all"):
+    plan = sgf.Plan.from_config(cfg, precision=precision, scheme=scheme)
+    c = torch.tensor(np.ascontiguousarray(cfg["coeffs"]).ravel(), dtype=torch.float64, device=DEV)
+    return plan, sgf.Factor(plan, c)
+
+
+def _t(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+SMALL = ["poisson2d_64", "rand2d_29_23_4", "grf3d_16", "rand3d_21_18_13_4", "grf3d_24",
+         "twophase3d_24", "grf3d_32"]
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_spmv_matches_oracle_operator(name):
+    cfg = _problem(name)
+    A, _, _ = _oracle(cfg)
+    plan, F = _gpu(cfg)
+    x = np.random.default_rng(1).standard_normal(plan.n)
+    y = F.spmv(_t(x)).cpu().numpy()
+    assert np.abs(y - A @ x).max() <= 1e-13 * np.abs(A @ x).max()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_ranks_match_oracle(name):
+    cfg = _problem(name)
+    A, H, O = _oracle(cfg)
+    plan, F = _gpu(cfg)
+    want = {}
+    for (t, node), v in O.comp_info.items():
+        want[(t, node)] = (v["m"], v["r"])
+    for li, lev in enumerate(H.levels[:-1]):
+        m, r = F.ranks(li, lev.nnodes)
+        for node in range(lev.nnodes):
+            if (lev.t, node) in want:
+                wm, wr = want[(lev.t, node)]
+                assert (m[node], min(r[node], wm)) == (wm, min(wr, wm)), (lev.t, node, m[node], r[node], wm, wr)
+                assert (r[node] < m[node]) == (wr < wm)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_apply_and_forward_match_oracle(name):
+    cfg = _problem(name)
+    A, H, O = _oracle(cfg)
+    plan, F = _gpu(cfg)
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        v = rng.standard_normal(plan.n)
+        y = F.apply(_t(v)).cpu().numpy()
+        yo = O.solve(v)
+        assert np.linalg.norm(y - yo) <= 1e-10 * np.linalg.norm(yo)
+        z = F.apply_forward(_t(v)).cpu().numpy()
+        zo = O.multiply(v)
+        assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "twophase3d_24"])
+def test_pcg_iterations_match_oracle(name):
+    cfg = _problem(name)
+    A, H, O = _oracle(cfg)
+    plan, F = _gpu(cfg)
+    b = si.rhs(plan.n, 0)
+    _, it_o, res_o = pcg(lambda v: A @ v, O.solve, b)
+    x, info = F.pcg(_t(b), rtol=1e-10, maxit=500)
+    assert abs(info["iterations"] - it_o) <= 1
+    assert info["rel_residual"] <= 1e-10
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(A @ xs - b) <= 1e-10 * np.linalg.norm(b) * 1.01
+
+
+def test_no_compression_is_exact_solve():
+    cfg = _problem("rand3d_21_18_13_4")
+    A, H, O = _oracle(cfg, scheme="none")
+    plan, F = _gpu(cfg, scheme="none")
+    b = np.random.default_rng(3).standard_normal(plan.n)
+    y = F.apply(_t(b)).cpu().numpy()
+    assert np.linalg.norm(A @ y - b) <= 1e-12 * np.linalg.norm(b)
+    x, info = F.pcg(_t(b))
+    assert info["iterations"] == 1
+
+
+@pytest.mark.parametrize("name", ["grf3d_32", "grf3d_64"])
+def test_preservation_on_gpu(name):
+    # A_l Pi = A Pi (Eq. (preserve-pi)) holds at any size
+    cfg = _problem(name)
+    plan, F = _gpu(cfg)
+    e = cfg["n"][0]
+    p = np.arange(plan.n)
+    xyz = np.stack([p % e, (p // e) % e, p // (e * e)], 1).astype(float)
+    Pi = eval_monomials(xyz, exponents(3, 2))
+    for k in range(Pi.shape[1]):
+        v = _t(Pi[:, k])
+        a = F.apply_forward(v)
+        b = F.spmv(v)
+        assert torch.linalg.norm(a - b).item() <= 1e-11 * torch.linalg.norm(b).item()
+
+
+def test_mixed_precision_converges_and_error_vs_oracle():
+    cfg = _problem("grf3d_32")
+    A, H, O = _oracle(cfg)
+    plan, F = _gpu(cfg, precision="mixed")
+    v = np.random.default_rng(5).standard_normal(plan.n)
+    y = F.apply(_t(v)).cpu().numpy()
+    yo = O.solve(v)
+    err = np.linalg.norm(y - yo) / np.linalg.norm(yo)
+    print(f"mixed apply rel err vs FP64 oracle: {err:.2e}")
+    assert err <= 1e-3
+    b = si.rhs(plan.n, 0)
+    x, info = F.pcg(_t(b), rtol=1e-10, maxit=500)
+    _, it_o, _ = pcg(lambda q: A @ q, O.solve, b)
+    print(f"mixed PCG {info['iterations']} it vs FP64 oracle {it_o}")
+    assert info["rel_residual"] <= 1e-10
+    assert info["iterations"] <= it_o + 10
+
+
+def test_host_buffer_path():
+    cfg = _problem("grf3d_16")
+    A, H, O = _oracle(cfg)
+    plan = sgf.Plan.from_config(cfg)
+    b = si.rhs(plan.n, 2, nrhs=2)
+    x, info = sgf.solve_host(plan, cfg["coeffs"].ravel(), b.ravel())
+    x = x.reshape(2, -1)
+    for j in range(2):
+        assert np.linalg.norm(A @ x[j] - b[j]) <= 1e-10 * np.linalg.norm(b[j]) * 1.01
+
+
+@pytest.mark.slow
+def test_full_size_64cube_apply_and_iterations():
+    cfg = _problem("grf3d_64")
+    A, H, O = _oracle(cfg)
+    plan, F = _gpu(cfg)
+    v = np.random.default_rng(11).standard_normal(plan.n)
+    y = F.apply(_t(v)).cpu().numpy()
+    yo = O.solve(v)
+    assert np.linalg.norm(y - yo) <= 1e-10 * np.linalg.norm(yo)
+    b = si.rhs(plan.n, 0)
+    x, info = F.pcg(_t(b), rtol=1e-10, maxit=500)
+    _, it_o, _ = pcg(lambda q: A @ q, O.solve, b)
+    assert abs(info["iterations"] - it_o) <= 1
+    assert info["rel_residual"] <= 1e-10
