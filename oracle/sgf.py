@@ -51,6 +51,11 @@ class Options:
     compress_from_level: int = 1
     basis: str = "poly"              # "poly" | "rbm"
     degree: int = 2
+    order: str = "sequential"        # "sequential" (Sec. 3.2 recursion) | "level"
+    # sensitivity probe for tests: perturb every entry of N by a relative
+    # rounding-level amount (seeded) before the pivoted QR
+    qr_noise: float = 0.0
+    qr_noise_seed: int = 0
 
 
 def _eligible(lev, i, dim, opts: Options) -> bool:
@@ -123,6 +128,7 @@ class SGFFactor:
             nbr[v].add(u)
         phi = {i: self.basis.evaluate(xyz[lev1.points[i]], lev1.box[i]) for i in range(lev1.nnodes)}
         rng = np.random.default_rng(self.order_seed) if self.order_seed is not None else None
+        noise_rng = np.random.default_rng(opts.qr_noise_seed)
 
         for li, lev in enumerate(H.levels):
             t = lev.t
@@ -164,27 +170,54 @@ class SGFFactor:
             order = [B for B in lev.separators() if _eligible(lev, B, H.dim, opts)]
             if rng is not None:
                 order = [order[k] for k in rng.permutation(len(order))]
+            # "level": every node sees the post-elimination matrix (see below)
+            src_blk, src_phi = (dict(blk), dict(phi)) if opts.order == "level" else (blk, phi)
+            level_q = {}
             for B in order:
                 m = sizes[B]
                 N_list = sorted(nbr[B])
-                L = self._chol(_get(blk, B, B))
-                Mh = [sla.solve_triangular(L, _get(blk, B, N), lower=True) for N in N_list]
-                Nmat = np.hstack([L.T @ phi[B]] + [Mh[k] @ phi[N] for k, N in enumerate(N_list)])
+                L = self._chol(_get(src_blk, B, B))
+                Mh = [sla.solve_triangular(L, _get(src_blk, B, N), lower=True) for N in N_list]
+                Nmat = np.hstack([L.T @ src_phi[B]] + [Mh[k] @ src_phi[N] for k, N in enumerate(N_list)])
+                if opts.qr_noise > 0:
+                    Nmat = Nmat * (1.0 + opts.qr_noise * noise_rng.standard_normal(Nmat.shape))
                 Q, R, _ = sla.qr(Nmat, pivoting=True)
                 d = np.abs(np.diag(R))
                 r = int(np.sum(d > opts.tau * d[0])) if d.size and d[0] > 0 else 0
                 info = dict(m=m, r=r, ncols=Nmat.shape[1], nnorm=float(np.linalg.norm(Nmat)),
+                            rdiag=d / d[0] if d.size and d[0] > 0 else d,
                             q2n=float(np.linalg.norm(Q[:, r:].T @ Nmat)) if r < m else 0.0,
                             compressed=r < m)
                 self.comp_info[(t, B)] = info
                 if r < m:
                     Q1 = Q[:, :r]
-                    blk[(B, B)] = np.eye(r)
-                    for k, N in enumerate(N_list):
-                        _set(blk, B, N, Q1.T @ Mh[k])
-                    phi[B] = Q1.T @ (L.T @ phi[B])
+                    if opts.order == "level":
+                        level_q[B] = (L, Q1)
+                    else:
+                        blk[(B, B)] = np.eye(r)
+                        for k, N in enumerate(N_list):
+                            _set(blk, B, N, Q1.T @ Mh[k])
+                    phi[B] = Q1.T @ (L.T @ src_phi[B])
                     sizes[B] = r
                     self.ops.append(("comp", t, B, L, Q, r))
+            if opts.order == "level":
+                # all compressions of the level from the post-elimination matrix:
+                # block (B, N) <- [Q1_B^T L_B^{-1}] A_BN [L_N^{-T} Q1_N], a factor
+                # for each compressed end (equal to the sequential recursion when
+                # the truncated part Q2^T N vanishes, Sec. 3.2)
+                for (u, v), X in list(src_blk.items()):
+                    if u == v:
+                        if u in level_q:
+                            blk[(u, u)] = np.eye(level_q[u][1].shape[1])
+                        continue
+                    Y = X
+                    if u in level_q:
+                        Lu, Qu = level_q[u]
+                        Y = Qu.T @ sla.solve_triangular(Lu, Y, lower=True)
+                    if v in level_q:
+                        Lv, Qv = level_q[v]
+                        Y = sla.solve_triangular(Lv, Y.T, lower=True).T @ Qv
+                    blk[(u, v)] = Y
             # 3. coarsen and merge
             nxt = H.levels[li + 1]
             parent, offset = {}, {}

@@ -174,6 +174,26 @@ def test_P6_compression_order_inside_a_level_does_not_matter():
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
 
 
+@pytest.mark.parametrize("name", ["grf3d_24", "twophase3d_24"])
+def test_P6_level_reading_matches_sequential_recursion(name):
+    # All compressions of a level from the post-elimination matrix (the form
+    # the device path batches) against the paper's node-after-node recursion:
+    # identical when Q2^T N vanishes, so they agree to rounding here.
+    cfg = si.config(name)
+    A = assemble(cfg)
+    H = build_hierarchy(cfg["n"], 3, 8, cfg["stencil"])
+    F1 = factorize(A, H, Options(degree=2))
+    F2 = factorize(A, H, Options(degree=2, order="level"))
+    assert F1.ranks() == F2.ranks()
+    v = np.random.default_rng(2).standard_normal(A.shape[0])
+    a, b = F1.solve(v), F2.solve(v)
+    assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
+    Pi = _global_poly(H, 2)
+    AP = A @ Pi
+    err = np.linalg.norm(np.stack([F2.multiply(Pi[:, k]) for k in range(Pi.shape[1])], 1) - AP)
+    assert err <= 1e-12 * np.linalg.norm(AP)
+
+
 def test_P7_iteration_trends_and_smooth_eigenvector_accuracy():
     its = {}
     for e in (16, 32):
