@@ -1,0 +1,413 @@
+"""Benchmark of the SGF hot path on GB300.
+
+One step = one whole factor + PCG solve to a 1e-10 relative residual
+(sgf_factor of a coefficient field, then sgf_pcg_solve of one right-hand
+side) on the 3D variable-coefficient diffusion workload: 7-point two-point-
+flux finite volumes on a 64^3 grid (n = 262,144), kappa = exp(g) with g a
+seeded Gaussian random field (correlation length 8 cells, std 2), Dirichlet
+on the x- face, Nest-All-All, piecewise-quadratic preservation, leaf 8.
+The headline is the mixed-precision path (FP32 factor and apply, FP64 PCG);
+the plain FP64 GPU path is timed beside it on the same inputs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own seeded instance (weak
+scaling, no data-path collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sgf_inputs as si  # noqa: E402
+
+METRIC = "factor+PCG time to 1e-10 residual, mixed vs FP64 GPU; serve p50/p99 latency"
+WORKLOAD = "grf3d_64"
+WORKLOAD_DESC = ("3D variable-coefficient diffusion, 7-pt TPFA on 64^3 (n=262144), kappa=exp(g), "
+                 "GRF l=8 std=2, Dirichlet x-, Nest-All-All, pcw-quadratic, leaf 8")
+SAMPLE_EDGE = 40       # CPU oracle sample (same recipe, smaller box), scaled by n
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+NOMINAL_SM = 152
+NOMINAL_MAX_MHZ = 2070.0
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (torchrun, one rank per GPU)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return dist if ws > 1 else None
+
+
+def reduce_max(value: float, dist=None, device=None) -> float:
+    """Max of a float over all ranks (identity on one rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist=None):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample(edge: int = SAMPLE_EDGE, seed: int = 0):
+    """Oracle factor + PCG on an edge^3 instance of the workload; (ms scaled to 64^3, detail)."""
+    from oracle.assemble import assemble
+    from oracle.partition import build_hierarchy
+    from oracle.pcg import pcg
+    from oracle.sgf import Options, factorize
+    cfg = si.config(f"grf3d_{edge}", seed)
+    A = assemble(cfg)
+    H = build_hierarchy(cfg["n"], 3, cfg["leaf"], cfg["stencil"])
+    b = si.rhs(A.shape[0], seed)
+    t0 = time.perf_counter()
+    F = factorize(A, H, Options(degree=cfg["degree"], order="level"))
+    _, it, res = pcg(lambda v: A @ v, F.solve, b)
+    dt = time.perf_counter() - t0
+    scale = (64 ** 3) / float(edge ** 3)
+    return 1e3 * dt * scale, dict(seconds=dt, iterations=it, rel_residual=res, edge=edge, scale=scale)
+
+
+def cpu_cores() -> int:
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ---------------------------------------------------------------------------
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_bound(name: str, precision: str, peaks: dict):
+    """(bound, unit, peak, note) for one kernel of the path."""
+    if name in ("k_gemv_n", "k_gemv_t", "k_spmv", "k_dot", "k_vector", "k_veccopy", "k_copy", "k_assemble"):
+        return "hbm", "GB/s", peaks["hbm_gbs"], "of measured HBM copy bandwidth"
+    # SIMT contractions: FP32 CUDA cores 152 SM x 128 lanes x 2 flop x 2070 MHz;
+    # FP64 is the nominal 1.25 TFLOP/s of GB300
+    if precision == "mixed":
+        return "alu", "TFLOP/s", NOMINAL_SM * 128 * 2 * NOMINAL_MAX_MHZ * 1e6 / 1e12, \
+            "FP32 SIMT peak from unit counts and max clock"
+    return "alu", "TFLOP/s", 1.25, "nominal GB300 FP64 rate"
+
+
+def traffic_from_profiles(kernel: str):
+    """dram bytes per launch recorded from an ncu capture of this kernel, if any."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    v = line.split(":", 1)[1].strip()
+                    return None if v == "null" else float(v)
+    except OSError:
+        pass
+    return None
+
+
+def roofline(prof: dict, precision: str, peaks: dict):
+    name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    bound, unit, peak, note = kernel_bound(name, precision, peaks)
+    if rec["ms"] <= 0 or rec["launches"] == 0:
+        return None
+    per_launch_ms = rec["ms"] / rec["launches"]
+    if bound == "hbm":
+        achieved = rec["bytes"] / (rec["ms"] * 1e-3) / 1e9
+    else:
+        achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
+    return {"kernel": name, "bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2),
+            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic_from_profiles(name),
+            "launches": rec["launches"], "avg_launch_ms": round(per_launch_ms, 5),
+            "share_of_step_kernels": None, "peak_note": note}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1907_03406_gb300 as sgf
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    cfg = si.config(WORKLOAD, seed=rank)
+    coeffs_h = np.ascontiguousarray(cfg["coeffs"].ravel())
+    b_h = si.rhs(int(np.prod(cfg["n"])), seed=rank)
+    coeffs = torch.tensor(coeffs_h, dtype=torch.float64, device=dev)
+    b = torch.tensor(b_h, dtype=torch.float64, device=dev)
+    plans = {p: sgf.Plan.from_config(cfg, precision=p) for p in ("mixed", "fp64")}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def one_step(plan):
+        F = sgf.Factor(plan, coeffs)
+        x, info = F.pcg(b, rtol=1e-10, maxit=500)
+        F.close()
+        return info
+
+    def timed(plan, steps, profile=False):
+        infos, total = [], 0.0
+        if profile:
+            sgf.profile_reset(timing=True)
+        for _ in range(steps):
+            flush.zero_()
+            barrier(dist)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(one_step(plan))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        prof = sgf.profile_read() if profile else None
+        return total, infos, prof
+
+    for _ in range(args.warmup):
+        one_step(plans["mixed"])
+    one_step(plans["fp64"])
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_mixed, infos_m, prof_m = timed(plans["mixed"], args.steps, profile=True)
+    clk = clocks.stop()
+    fp64_steps = max(1, min(args.steps, 3))
+    ms_fp64, infos_d, prof_d = timed(plans["fp64"], fp64_steps, profile=True)
+
+    # end to end through the host-buffer C ABI call, pinned host memory
+    pc = torch.tensor(coeffs_h, dtype=torch.float64).pin_memory()
+    pb = torch.tensor(b_h, dtype=torch.float64).pin_memory()
+    px = torch.empty_like(pb).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sgf.solve_host_ptr(plans["mixed"], pc.data_ptr(), pb.data_ptr(), px.data_ptr(), 1)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+
+    per_step = ms_mixed / args.steps
+    per_step_fp64 = ms_fp64 / fp64_steps
+    per_step = reduce_max(per_step, dist, dev)
+    per_step_fp64 = reduce_max(per_step_fp64, dist, dev)
+    e2e = reduce_max(statistics.median(e2e_ms), dist, dev)
+    launches = sum(v["launches"] for v in prof_m.values())
+
+    if rank != 0:
+        barrier(dist)
+        return
+    peaks, peak_kind = load_peaks()
+    roof = roofline(prof_m, "mixed", peaks)
+    if roof is not None:
+        total_k = sum(v["ms"] for v in prof_m.values())
+        roof["share_of_step_kernels"] = round(prof_m[roof["kernel"]]["ms"] / total_k, 4) if total_k else None
+        roof["peak_source"] = peak_kind
+    roof_d = roofline(prof_d, "fp64", peaks)
+    n = int(np.prod(cfg["n"]))
+    line = {
+        "metric": METRIC,
+        "value": round(per_step, 3),
+        "unit": "ms",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(per_step, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "mixed (FP32 factor/apply, FP64 PCG/SpMV/dots)",
+                   "n": n, "rtol": 1e-10, "per_rank_instances": 1, "parallelism": f"replicas x{ws}",
+                   "l2": "256 MB buffer written between timed steps; factor data > L2"},
+        "iterations": [i["iterations"] for i in infos_m],
+        "rel_residual": max(i["rel_residual"] for i in infos_m),
+        "fp64": {"ms_per_step": round(per_step_fp64, 3), "steps": fp64_steps,
+                 "iterations": [i["iterations"] for i in infos_d],
+                 "rel_residual": max(i["rel_residual"] for i in infos_d),
+                 "speedup_mixed_over_fp64": round(per_step_fp64 / per_step, 3),
+                 "roofline": roof_d},
+        "solves_per_s": round(ws * 1e3 / per_step, 3),
+        "roofline": roof,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof_m.items() if v["launches"]},
+        "gpu_launches": launches,
+        "e2e": {"value": round(e2e, 3), "unit": "ms", "h2d_bytes_per_step": 8 * (coeffs_h.size + b_h.size),
+                "d2h_bytes_per_step": 8 * b_h.size},
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu_ms, det = oracle_sample()
+        line["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"oracle factor+PCG on the {det['edge']}^3 instance of the same recipe "
+                                          f"({det['seconds']:.1f} s, {det['iterations']} it), scaled by n x{det['scale']:.2f}"}
+    print(json.dumps(line), flush=True)
+    barrier(dist)
+
+
+def run_ncu(args):
+    """One step inside an NVTX range "sgf_step" after warm-up steps outside it
+    (for ncu --nvtx --nvtx-include sgf_step/)."""
+    import torch
+    import paper_1907_03406_gb300 as sgf
+    dev = torch.device("cuda", 0)
+    cfg = si.config(args.workload, seed=0)
+    coeffs = torch.tensor(np.ascontiguousarray(cfg["coeffs"].ravel()), dtype=torch.float64, device=dev)
+    b = torch.tensor(si.rhs(int(np.prod(cfg["n"])), 0), dtype=torch.float64, device=dev)
+    plan = sgf.Plan.from_config(cfg, precision=args.precision)
+
+    def step():
+        F = sgf.Factor(plan, coeffs)
+        _, info = F.pcg(b, rtol=1e-10, maxit=500)
+        F.close()
+        return info
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("sgf_step")
+    info = step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"ncu_step": args.workload, "precision": args.precision, **info}), flush=True)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    det = None
+    for k in range(args.warmup + args.steps):
+        ms, det = oracle_sample(seed=k % 2)
+        if k >= args.warmup:
+            vals.append(ms)
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "precision": "fp64 CPU oracle"},
+            "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"each step: oracle factor+PCG on the {det['edge']}^3 instance, "
+                                       f"scaled by n x{det['scale']:.2f}"},
+            "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu", action="store_true", help="one step in an NVTX range, for ncu")
+    ap.add_argument("--workload", default=WORKLOAD, help="ncu mode: grf3d_<edge> / twophase3d_<edge>")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    args = ap.parse_args(argv)
+    if args.ncu:
+        return run_ncu(args)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -186,6 +186,18 @@ const char* sgf_last_error(void);
 int64_t sgf_dry_run_violations(int reset);
 const char* sgf_dry_run_report(void);
 
+/* Launch accounting for benchmarks.  Kernel kinds 0..10 are named by
+ * sgf_profile_kind_name (k_gemm, k_diag, k_copy, k_qrcp, k_gemv_n, k_gemv_t,
+ * k_veccopy, k_assemble, k_spmv, k_dot, k_vector).  sgf_profile_reset clears
+ * the counters; with timing != 0 every later launch is bracketed by CUDA
+ * events on its own stream.  sgf_profile_read (synchronizes on the recorded
+ * events) returns, for one kind, the launches since the reset, their summed
+ * device time in ms (0 without timing) and the algorithmic flops and bytes
+ * the host attached to them.  Not thread-safe with concurrent factors.      */
+void sgf_profile_reset(int timing);
+int sgf_profile_read(int kind, int64_t* launches, double* ms, double* flops, double* bytes);
+const char* sgf_profile_kind_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -202,3 +202,33 @@ def solve_host(plan: Plan, coeffs: np.ndarray, b: np.ndarray, rtol=1e-10, maxit=
                             _stream_ptr(stream), C.byref(info))
     _check(rc, "sgf_solve_host")
     return x, dict(iterations=info.iterations, rel_residual=info.rel_residual, seconds=info.seconds)
+
+
+def profile_reset(timing: bool = False):
+    """Clear the launch counters; with timing, bracket every launch with CUDA events."""
+    L.load().sgf_profile_reset(1 if timing else 0)
+
+
+def profile_read() -> dict:
+    """{kernel name: dict(launches, ms, flops, bytes)} since the last reset."""
+    lib = L.load()
+    out = {}
+    for k in range(64):
+        name = lib.sgf_profile_kind_name(k).decode()
+        if name == "?":
+            break
+        n = C.c_int64()
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        _check(lib.sgf_profile_read(k, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)), "profile_read")
+        out[name] = dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+    return out
+
+
+def solve_host_ptr(plan: Plan, coeffs_ptr: int, b_ptr: int, x_ptr: int, nrhs: int, rtol=1e-10,
+                   maxit=500, stream=None):
+    """sgf_solve_host on raw host pointers (e.g. pinned torch CPU tensors)."""
+    info = L.sgf_solve_info()
+    rc = plan._lib.sgf_solve_host(plan.handle, C.c_void_p(coeffs_ptr), C.c_void_p(b_ptr), C.c_void_p(x_ptr),
+                                  int(nrhs), float(rtol), int(maxit), _stream_ptr(stream), C.byref(info))
+    _check(rc, "sgf_solve_host")
+    return dict(iterations=info.iterations, rel_residual=info.rel_residual, seconds=info.seconds)

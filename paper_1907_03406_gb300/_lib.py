@@ -52,6 +52,9 @@ SIGNATURES = {
     "sgf_last_error": (C.c_char_p, []),
     "sgf_dry_run_violations": (C.c_int64, [_I]),
     "sgf_dry_run_report": (C.c_char_p, []),
+    "sgf_profile_reset": (None, [_I]),
+    "sgf_profile_read": (_I, [_I, _I64P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sgf_profile_kind_name": (C.c_char_p, [_I]),
 }
 
 _lib = None

@@ -9,6 +9,7 @@
 
 #include "devmem.h"
 #include "factor.h"
+#include "prof.h"
 #include "sgf.h"
 #include "sgf_internal.h"
 
@@ -268,4 +269,16 @@ const char* sgf_dry_run_report(void) {
   s = sgf::dry_run_report();
   return s.c_str();
 }
+}
+
+extern "C" {
+void sgf_profile_reset(int timing) { sgf::prof_reset(timing); }
+int sgf_profile_read(int kind, int64_t* launches, double* ms, double* flops, double* bytes) {
+  long long l = 0;
+  int rc = sgf::prof_read(kind, &l, ms, flops, bytes);
+  if (rc) return SGF_ERR_INVALID_ARG;
+  if (launches) *launches = l;
+  return SGF_OK;
+}
+const char* sgf_profile_kind_name(int kind) { return sgf::prof_name(kind); }
 }

@@ -43,6 +43,7 @@
 
 #include "devmem.h"
 #include "factor.h"
+#include "prof.h"
 
 namespace sgf {
 
@@ -133,9 +134,17 @@ struct GemmList {
   }
   void emit(Batch& b, cudaStream_t s) {
     if (t.empty()) return;
+    double fl = 0, by = 0;
+    for (const auto& g : t)
+      for (int k = g.c_begin; k < g.c_begin + g.c_count; ++k) {
+        fl += 2.0 * g.M * g.N * c[k].K;
+        by += (double)sizeof(T) * ((double)g.M * c[k].K + (double)c[k].K * g.N);
+      }
+    for (const auto& g : t) by += (double)sizeof(T) * g.M * g.N * (g.beta ? 2 : 1);
     const size_t ot = b.push(t), oc = b.push(c);
     const int n = (int)t.size();
     b.launches.push_back([=](const char* d) {
+      prof_work(fl, by);
       launch_gemm<T>((const GemmTask<T>*)(d + ot), (const GemmContrib<T>*)(d + oc), n, s);
     });
     t.clear();
@@ -322,10 +331,26 @@ struct GemvList {
   }
   void emit(Program<T>& P) {
     if (t.empty()) return;
+    double fl = 0, by = 0;
+    for (const auto& g : t) {
+      by += (double)sizeof(T) * g.M * (g.beta ? 2 : 1);
+      for (int k = g.c_begin; k < g.c_begin + g.c_count; ++k) {
+        // elements of A read: the lower-triangular ones only when tri is set
+        double el = (double)g.M * c[k].K;
+        if (c[k].tri) {
+          const double lo = c[k].tri - 1, hi = lo + g.M;  // absolute rows / columns of the chunk
+          el = trans ? (double)g.M * c[k].K - 0.5 * (hi * (hi - 1) - lo * (lo - 1))
+                     : 0.5 * ((hi) * (hi + 1) - lo * (lo + 1));
+        }
+        fl += 2.0 * el;
+        by += (double)sizeof(T) * (el + c[k].K * (c[k].x2 ? 2.0 : 1.0));
+      }
+    }
     const size_t ot = P.b.push(t), oc = P.b.push(c);
     const int n = (int)t.size();
     const bool tr = trans;
     P.ops.push_back([=](const char* d, cudaStream_t s) {
+      prof_work(fl, by);
       if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, s);
       else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, s);
     });

@@ -22,6 +22,7 @@
 
 #include "devmem.h"
 #include "kernels.h"
+#include "prof.h"
 
 namespace sgf {
 
@@ -540,7 +541,9 @@ void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* cons, int n, cu
     }
     return;
   }
-  if (n > 0) k_gemm<T><<<n, kThreads, 0, s>>>(tasks, cons);
+  if (n <= 0) return;
+  ProfScope ps(P_GEMM, s);
+  k_gemm<T><<<n, kThreads, 0, s>>>(tasks, cons);
 }
 
 template <typename T>
@@ -560,6 +563,7 @@ void launch_diag(const DiagTask<T>* tasks, int n, DevStatus* st, int level, cuda
     cudaFuncSetAttribute(k_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
+  ProfScope ps(P_DIAG, s);
   k_diag<T><<<n, kThreads, sm, s>>>(tasks, st, level);
 }
 
@@ -575,7 +579,9 @@ void launch_copy(const CopyTask<S, D>* tasks, int n, cudaStream_t s) {
     }
     return;
   }
-  if (n > 0) k_copy<S, D><<<n, kThreads, 0, s>>>(tasks);
+  if (n <= 0) return;
+  ProfScope ps(P_COPY, s);
+  k_copy<S, D><<<n, kThreads, 0, s>>>(tasks);
 }
 
 template <typename T>
@@ -595,6 +601,7 @@ void launch_qrcp(const QrTask<T>* tasks, int n, int* ranks, double tau, int max_
   const int kmin = max_m < max_c ? max_m : max_c;
   const size_t sm = sizeof(double) * (size_t)(max_c + kmin) + sizeof(T) * (size_t)max_m + 16;
   cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ProfScope ps(P_QR, s);
   k_qrcp<T><<<n, kThreads, sm, s>>>(tasks, ranks, tau, st, level);
 }
 
@@ -617,13 +624,17 @@ static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int
 template <typename T>
 void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, cudaStream_t s) {
   if (dry_run()) return check_gemv(tasks, cons, n, false);
-  if (n > 0) k_gemv_n<T><<<n, kThreads, 0, s>>>(tasks, cons);
+  if (n <= 0) return;
+  ProfScope ps(P_GEMV_N, s);
+  k_gemv_n<T><<<n, kThreads, 0, s>>>(tasks, cons);
 }
 
 template <typename T>
 void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, cudaStream_t s) {
   if (dry_run()) return check_gemv(tasks, cons, n, true);
-  if (n > 0) k_gemv_t<T><<<n, kThreads, 0, s>>>(tasks, cons);
+  if (n <= 0) return;
+  ProfScope ps(P_GEMV_T, s);
+  k_gemv_t<T><<<n, kThreads, 0, s>>>(tasks, cons);
 }
 
 template <typename T>
@@ -635,7 +646,9 @@ void launch_veccopy(const VecCopyTask* tasks, int n, const T* src, T* dst, cudaS
     }
     return;
   }
-  if (n > 0) k_veccopy<T><<<n, kThreads, 0, s>>>(tasks, src, dst);
+  if (n <= 0) return;
+  ProfScope ps(P_VECCOPY, s);
+  k_veccopy<T><<<n, kThreads, 0, s>>>(tasks, src, dst);
 }
 
 template <typename T>
@@ -648,6 +661,7 @@ void launch_assemble_scalar(const double* coef, int nx, int ny, int nz, unsigned
     for (double* a : {sd, sx, sy, sz}) check_range(a, 8 * n, "assemble stencil arrays");
     return;
   }
+  ProfScope ps(P_ASSEMBLE, s);
   k_assemble<T><<<blocks_for(n), kThreads, 0, s>>>(coef, nx, ny, nz, dm, w, map, dgsz, dg, up, sd, sx, sy, sz);
 }
 
@@ -655,12 +669,16 @@ void launch_spmv_stencil(const double* sd, const double* sx, const double* sy, c
                          int nx, int ny, int nz, const double* x, double* y, cudaStream_t s) {
   const int64_t n = (int64_t)nx * ny * nz;
   if (dry_run()) return;
+  prof_work(13.0 * n, 48.0 * n);
+  ProfScope ps(P_SPMV, s);
   k_spmv<<<blocks_for(n), kThreads, 0, s>>>(sd, sx, sy, sz, nx, ny, nz, x, y);
 }
 
 void launch_dot(const double* a, const double* b, int64_t n, double* partials, double* result,
                 cudaStream_t s) {
   if (dry_run()) return;
+  prof_work(2.0 * n, 16.0 * n);
+  ProfScope ps(P_DOT, s);
   k_dot_partial<<<kDotBlocks, kThreads, 0, s>>>(a, b, n, partials);
   k_dot_final<<<1, kThreads, 0, s>>>(partials, kDotBlocks, result);
 }
@@ -672,7 +690,10 @@ void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, cu
     check_range(dst, sizeof(T) * n, "gather dst");
     return;
   }
-  if (n > 0) k_gather<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n);
+  if (n <= 0) return;
+  prof_work(0, (16.0 + sizeof(T)) * n);
+  ProfScope ps(P_VEC, s);
+  k_gather<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n);
 }
 template <typename T>
 void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, cudaStream_t s) {
@@ -681,16 +702,25 @@ void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, c
     check_range(src, sizeof(T) * n, "scatter src");
     return;
   }
-  if (n > 0) k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n);
+  if (n <= 0) return;
+  prof_work(0, (16.0 + sizeof(T)) * n);
+  ProfScope ps(P_VEC, s);
+  k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n);
 }
 
 void launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s) {
   if (dry_run()) return;
-  if (n > 0) k_axpy<<<blocks_for(n), kThreads, 0, s>>>(a, x, y, n);
+  if (n <= 0) return;
+  prof_work(2.0 * n, 24.0 * n);
+  ProfScope ps(P_VEC, s);
+  k_axpy<<<blocks_for(n), kThreads, 0, s>>>(a, x, y, n);
 }
 void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s) {
   if (dry_run()) return;
-  if (n > 0) k_xpay<<<blocks_for(n), kThreads, 0, s>>>(z, b, p, n);
+  if (n <= 0) return;
+  prof_work(2.0 * n, 24.0 * n);
+  ProfScope ps(P_VEC, s);
+  k_xpay<<<blocks_for(n), kThreads, 0, s>>>(z, b, p, n);
 }
 
 #define SGF_INST(T)                                                                              \

@@ -1,0 +1,113 @@
+// Launch accounting (see prof.h).
+#include "prof.h"
+
+#include <mutex>
+#include <vector>
+
+namespace sgf {
+
+namespace {
+struct Acc {
+  long long launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+struct Pending {
+  cudaEvent_t a, b;
+  int kind;
+};
+struct State {
+  std::mutex mu;
+  Acc acc[P_NKINDS];
+  int timing = 0;
+  double next_flops = 0, next_bytes = 0;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+};
+State& st() {
+  static State s;
+  return s;
+}
+cudaEvent_t get_event(State& S) {
+  if (!S.pool.empty()) {
+    cudaEvent_t e = S.pool.back();
+    S.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+void drain(State& S) {
+  for (auto& p : S.pending) {
+    cudaEventSynchronize(p.b);
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) S.acc[p.kind].ms += ms;
+    S.pool.push_back(p.a);
+    S.pool.push_back(p.b);
+  }
+  S.pending.clear();
+}
+}  // namespace
+
+void prof_work(double flops, double bytes) {
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  S.next_flops += flops;
+  S.next_bytes += bytes;
+}
+
+ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  Acc& a = S.acc[kind];
+  a.launches++;
+  a.flops += S.next_flops;
+  a.bytes += S.next_bytes;
+  S.next_flops = S.next_bytes = 0;
+  if (S.timing) {
+    Pending p;
+    p.a = get_event(S);
+    p.b = get_event(S);
+    p.kind = kind;
+    cudaEventRecord(p.a, s);
+    S.pending.push_back(p);
+    slot_ = (int)S.pending.size() - 1;
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (slot_ < 0) return;
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  if (slot_ < (int)S.pending.size()) cudaEventRecord(S.pending[slot_].b, s_);
+}
+
+void prof_reset(int timing) {
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  drain(S);
+  for (auto& a : S.acc) a = Acc();
+  S.timing = timing;
+  S.next_flops = S.next_bytes = 0;
+}
+
+int prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes) {
+  if (kind < 0 || kind >= P_NKINDS) return -1;
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  drain(S);
+  const Acc& a = S.acc[kind];
+  if (launches) *launches = a.launches;
+  if (ms) *ms = a.ms;
+  if (flops) *flops = a.flops;
+  if (bytes) *bytes = a.bytes;
+  return 0;
+}
+
+const char* prof_name(int kind) {
+  static const char* n[P_NKINDS] = {"k_gemm",   "k_diag",     "k_copy", "k_qrcp", "k_gemv_n", "k_gemv_t",
+                                    "k_veccopy", "k_assemble", "k_spmv", "k_dot",  "k_vector"};
+  return (kind >= 0 && kind < P_NKINDS) ? n[kind] : "?";
+}
+
+}  // namespace sgf

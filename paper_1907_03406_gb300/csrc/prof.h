@@ -1,0 +1,34 @@
+// Launch accounting for the benchmark: per kernel kind, the number of
+// launches, the algorithmic flops / bytes the host attached to them and, when
+// timing is on, their device time from CUDA events recorded on the launching
+// stream around each launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sgf {
+
+enum ProfKind {
+  P_GEMM = 0, P_DIAG, P_COPY, P_QR, P_GEMV_N, P_GEMV_T, P_VECCOPY, P_ASSEMBLE, P_SPMV, P_DOT,
+  P_VEC, P_NKINDS
+};
+
+// work of the next launch (set by the code that built its tasks)
+void prof_work(double flops, double bytes);
+
+class ProfScope {
+ public:
+  ProfScope(int kind, cudaStream_t s);
+  ~ProfScope();
+
+ private:
+  int kind_;
+  cudaStream_t s_;
+  int slot_;
+};
+
+void prof_reset(int timing);
+int prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes);
+const char* prof_name(int kind);
+
+}  // namespace sgf
