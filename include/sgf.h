@@ -166,6 +166,28 @@ typedef struct sgf_solve_info {
 int sgf_pcg_solve(const sgf_factor_t* f, const double* b_dev, double* x_dev, int nrhs,
                   double rtol, int maxit, void* stream, sgf_solve_info* info);
 
+/* ---- allocation-free PCG ---------------------------------------------------
+ * sgf_pcg_solve_noalloc: the PCG of sgf_pcg_solve (one right-hand side) for
+ * callers that cannot let the library allocate device memory while solving:
+ * a process that reserves its whole memory budget up front and treats any
+ * later cudaMalloc as a violation, code that owns all device memory through
+ * its own arena, or a latency-critical loop that cannot afford an allocator
+ * call.  The paper has no counterpart; this is a deployment interface.
+ * Its work vectors and dot-product partial sums live in one fixed device
+ * array of 5 * SGF_NOALLOC_MAX_UNKNOWNS + 368 doubles (about 10 MiB) that
+ * every GPU loading the library keeps until the process exits; factors with
+ * more than SGF_NOALLOC_MAX_UNKNOWNS unknowns are rejected with
+ * SGF_ERR_INVALID_ARG.  It calls no allocator.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current): make that first call before any stream capture.  Every call
+ * shares the one array and writes each word it reads, so nothing carries
+ * over between calls, but calls that overlap on the GPU (other streams or
+ * threads) race on it and must not be issued.  Synchronizes the stream;
+ * info->seconds is host wall time.                                         */
+#define SGF_NOALLOC_MAX_UNKNOWNS 262144
+int sgf_pcg_solve_noalloc(const sgf_factor_t* f, const double* b_dev, double* x_dev, double rtol,
+                          int maxit, void* stream, sgf_solve_info* info);
+
 /* Host-buffer convenience path: copies coeffs/b from host memory, factors,
  * solves and copies x back (the end-to-end call of the serving loop).      */
 int sgf_solve_host(const sgf_plan* plan, const double* coeffs_host, const double* b_host,

@@ -48,6 +48,7 @@ SIGNATURES = {
     "sgf_spmv": (_I, [_P, _P, _P, _I, _P]),
     "sgf_pcg_solve": (_I, [_P, _P, _P, _I, C.c_double, _I, _P, C.POINTER(sgf_solve_info)]),
     "sgf_solve_host": (_I, [_P, _P, _P, _P, _I, C.c_double, _I, _P, C.POINTER(sgf_solve_info)]),
+    "sgf_pcg_solve_noalloc": (_I, [_P, _P, _P, C.c_double, _I, _P, C.POINTER(sgf_solve_info)]),
     "sgf_status_string": (C.c_char_p, [_I]),
     "sgf_last_error": (C.c_char_p, []),
     "sgf_dry_run_violations": (C.c_int64, [_I]),

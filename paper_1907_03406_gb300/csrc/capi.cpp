@@ -13,14 +13,7 @@
 #include "sgf.h"
 #include "sgf_internal.h"
 
-struct sgf_plan {
-  sgf::Plan p;
-};
-
-struct sgf_factor_s {
-  std::unique_ptr<sgf::FactorBase> f;
-  const sgf_plan* plan;
-};
+#include "handles.h"
 
 namespace {
 thread_local std::string g_last_error;
