@@ -441,6 +441,60 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
     }
   }
 
+  // ---- basis columns that can be nonzero on each node -------------------
+  for (auto& L : P.lev) {
+    L.act.assign(L.nnodes, 0);
+    for (int i = 0; i < L.nnodes; ++i) {
+      int cnt = 0;
+      for (const auto& e : ex) {
+        bool ok = true;
+        for (int a = 0; a < 3; ++a)
+          if (e[a] > 0 && L.box[6 * i + a] == L.box[6 * i + 3 + a]) ok = false;
+        cnt += ok;
+      }
+      L.act[i] = cnt;
+    }
+  }
+
+  // ---- level-1 assembly destinations (scalar stencils) ------------------
+  {
+    const LevelSym& L1 = P.lev[0];
+    std::vector<int> m1(L1.nnodes);
+    for (int i = 0; i < L1.nnodes; ++i) m1[i] = (L1.pt_ptr[i + 1] - L1.pt_ptr[i]) * P.dof;
+    LevelLayout lay;
+    build_layout(L1, m1, lay);
+    std::vector<int> node_of(P.npts), lpos(P.npts);
+    P.perm1.assign(P.npts, 0);
+    for (int u = 0; u < L1.nnodes; ++u)
+      for (int k = L1.pt_ptr[u]; k < L1.pt_ptr[u + 1]; ++k) {
+        const int p = L1.pt_idx[k];
+        node_of[p] = u;
+        lpos[p] = k - L1.pt_ptr[u];
+        P.perm1[lay.vec_off[u] + lpos[p]] = p;
+      }
+    P.asm_map.assign(P.npts * 7, -1);
+    const int64_t nxy = (int64_t)P.nx * P.ny;
+    for (int64_t p = 0; p < P.npts; ++p) {
+      const int x = (int)(p % P.nx), y = (int)((p / P.nx) % P.ny), z = (int)(p / nxy);
+      const int u = node_of[p], lp = lpos[p];
+      const int64_t nbq[6] = {x > 0 ? p - 1 : -1, x < P.nx - 1 ? p + 1 : -1,
+                              y > 0 ? p - P.nx : -1, y < P.ny - 1 ? p + P.nx : -1,
+                              z > 0 ? p - nxy : -1, z < P.nz - 1 ? p + nxy : -1};
+      for (int q = 0; q < 6; ++q) {
+        if (nbq[q] < 0) continue;
+        const int v = node_of[nbq[q]], lq = lpos[nbq[q]];
+        if (u == v) {
+          P.asm_map[p * 7 + q] = lay.dg_off[u] + lp + (int64_t)lq * m1[u];
+        } else if (u < v) {
+          const int col = lay.col_of(u, v);
+          if (col < 0) { err = "internal: missing level-1 block"; return SGF_ERR_INVALID_ARG; }
+          P.asm_map[p * 7 + q] = lay.dg_size + lay.up_off[u] + (int64_t)(col + lq) * m1[u] + lp;
+        }
+      }
+      P.asm_map[p * 7 + 6] = lay.dg_off[u] + lp + (int64_t)lp * m1[u];
+    }
+  }
+
   // ---- structural size bounds (no compression) -------------------------
   P.mcap.resize(P.lev.size());
   for (size_t li = 0; li < P.lev.size(); ++li) {

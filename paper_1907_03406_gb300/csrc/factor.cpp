@@ -37,7 +37,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <numeric>
 
@@ -48,22 +51,45 @@
 namespace sgf {
 
 void Batch::run(cudaStream_t s) {
+  char* d = nullptr;
   if (!host.empty()) {
-    if (host.size() > cap) {
-      if (dev) dev_free_async(dev, s);
-      dev = nullptr;
-      size_t want = std::max(host.size(), size_t(1) << 20);
-      dev = (char*)dev_malloc_async(want, s);
-      cap = want;
+    if (dry_run()) {
+      d = host.data();
+    } else {
+      // pinned staging, two buffers in turn: a buffer is refilled only after
+      // the copy that last read it has completed
+      const int i = cur;
+      cur ^= 1;
+      if (ev[i]) SGF_CK(cudaEventSynchronize(ev[i]));
+      else SGF_CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+      if (pincap[i] < host.size()) {
+        if (pin[i]) cudaFreeHost(pin[i]);
+        pincap[i] = std::max(host.size() + host.size() / 2, size_t(1) << 20);
+        SGF_CK(cudaHostAlloc((void**)&pin[i], pincap[i], cudaHostAllocDefault));
+      }
+      std::memcpy(pin[i], host.data(), host.size());
+      d = (char*)dev_malloc_async(host.size(), s);
+      SGF_CK(cudaMemcpyAsync(d, pin[i], host.size(), cudaMemcpyHostToDevice, s));
+      SGF_CK(cudaEventRecord(ev[i], s));
     }
-    dev_h2d(dev, host.data(), host.size(), s);
   }
-  // in dry-run mode the launch wrappers validate the host copy of the tasks
-  const char* base = dry_run() ? host.data() : dev;
-  for (auto& f : launches) f(base);
-  if (!dry_run()) SGF_CK(cudaGetLastError());
+  for (auto& f : launches) f(d);
+  if (!dry_run()) {
+    SGF_CK(cudaGetLastError());
+    if (d) dev_free_async(d, s);   // stream ordered, after the launches above
+  }
   host.clear();
   launches.clear();
+}
+
+Batch::~Batch() {
+  for (int i = 0; i < 2; ++i) {
+    if (ev[i]) {
+      cudaEventSynchronize(ev[i]);
+      cudaEventDestroy(ev[i]);
+    }
+    if (pin[i]) cudaFreeHost(pin[i]);
+  }
 }
 
 void Batch::upload_persistent(cudaStream_t s) {
@@ -103,7 +129,13 @@ template <typename T>
 struct GemmList {
   std::vector<GemmTask<T>> t;
   std::vector<GemmContrib<T>> c;
+  void add(T* C, int ldc, int M, int N, T alpha, int beta, std::initializer_list<Spec<T>> specs) {
+    add_range(C, ldc, M, N, alpha, beta, specs.begin(), specs.end());
+  }
   void add(T* C, int ldc, int M, int N, T alpha, int beta, const std::vector<Spec<T>>& specs) {
+    add_range(C, ldc, M, N, alpha, beta, specs.data(), specs.data() + specs.size());
+  }
+  void add_range(T* C, int ldc, int M, int N, T alpha, int beta, const Spec<T>* sb, const Spec<T>* se) {
     if (M <= 0 || N <= 0) return;
     for (int j0 = 0; j0 < N; j0 += kTile)
       for (int i0 = 0; i0 < M; i0 += kTile) {
@@ -116,7 +148,8 @@ struct GemmList {
         g.alpha = alpha;
         g.beta = beta;
         int cnt = 0;
-        for (const auto& s : specs) {
+        for (const Spec<T>* sp = sb; sp != se; ++sp) {
+          const Spec<T>& s = *sp;
           if (s.K <= 0) continue;
           GemmContrib<T> q;
           q.A = s.ta ? s.A + (size_t)i0 * s.lda : s.A + i0;
@@ -131,6 +164,14 @@ struct GemmList {
         g.c_count = cnt;
         t.push_back(g);
       }
+  }
+  // C[M x N] = Li B with Li lower triangular (M x M): row tile i0 needs only
+  // the first min(M, i0 + 64) rows of B
+  void add_lowtri(T* C, int ldc, int M, int N, const T* Li, int ldli, const T* B, int ldb) {
+    for (int i0 = 0; i0 < M; i0 += kTile) {
+      const int K = std::min(M, i0 + kTile);
+      add(C + i0, ldc, std::min(kTile, M - i0), N, T(1), 0, {{Li + i0, ldli, false, B, ldb, false, K}});
+    }
   }
   void emit(Batch& b, cudaStream_t s) {
     if (t.empty()) return;
@@ -196,7 +237,26 @@ struct Front {
 // Blocked right-looking Cholesky of D with the triangular solves of the panel
 // and of the identity (giving L^{-1}), batched over all fronts.
 template <typename T>
-void run_fronts(const std::vector<Front<T>>& F, Batch& b, cudaStream_t s, DevStatus* st, int level) {
+void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level) {
+  // small fronts without a panel: one CTA does the whole sweep
+  std::vector<FrontTask<T>> small;
+  std::vector<Front<T>> F;
+  for (const auto& f : Fall) {
+    // beyond kFrontSmall the tile sweep spread over many CTAs wins: one CTA
+    // pays a memory latency per tile product
+    if (f.s == 0 && f.m <= kFrontSmall) small.push_back({f.D, f.Li, f.m, f.node});
+    else F.push_back(f);
+  }
+  if (!small.empty()) {
+    const size_t of = b.push(small);
+    const int nf = (int)small.size();
+    double fl = 0;
+    for (const auto& f : small) fl += 2.0 * (2.0 / 3.0) * f.m * (double)f.m * f.m;
+    b.launches.push_back([=](const char* d) {
+      prof_work(fl, 0);
+      launch_front<T>((const FrontTask<T>*)(d + of), nf, st, level, s);
+    });
+  }
   int kmax = 0;
   for (const auto& f : F) kmax = std::max(kmax, (f.m + kTile - 1) / kTile);
   for (int k = 0; k < kmax; ++k) {
@@ -236,7 +296,6 @@ void run_fronts(const std::vector<Front<T>>& F, Batch& b, cudaStream_t s, DevSta
     }
     panel.emit(b, s);
     update.emit(b, s);
-    b.run(s);
   }
 }
 
@@ -280,11 +339,15 @@ struct LevelRec {
   std::vector<SepRec<T>> sep;
 };
 
-// one recorded launch of an apply program
+// a fixed sequence of batched launches (replayed as one CUDA graph)
 template <typename T>
 struct Program {
   Batch b;
   std::vector<std::function<void(const char*, cudaStream_t)>> ops;
+  struct Acct { int kind; double flops, bytes; };
+  std::vector<Acct> acct;      // launch accounting added per replay
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
 };
 
 template <typename T>
@@ -349,6 +412,7 @@ struct GemvList {
     const size_t ot = P.b.push(t), oc = P.b.push(c);
     const int n = (int)t.size();
     const bool tr = trans;
+    P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl, by});
     P.ops.push_back([=](const char* d, cudaStream_t s) {
       prof_work(fl, by);
       if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, s);
@@ -379,7 +443,9 @@ class FactorImpl final : public FactorBase {
     dev_memset(st_, 0, sizeof(DevStatus), s);
     try {
       build(coeffs, s);
+      trace(s, 0, "factor levels done");
       build_programs(s);
+      trace(s, 0, "apply programs");
     } catch (...) {
       release();
       throw;
@@ -398,7 +464,7 @@ class FactorImpl final : public FactorBase {
   std::vector<void*> keep_;
   DevStatus* st_ = nullptr;
   double *sd_ = nullptr, *sx_ = nullptr, *sy_ = nullptr, *sz_ = nullptr;
-  int64_t* perm1_ = nullptr;
+  const int64_t* perm1_ = nullptr;
   std::vector<LevelRec<T>> lev_;
   int mtop_ = 0;
   T *Ltop_ = nullptr, *Litop_ = nullptr;
@@ -415,6 +481,12 @@ class FactorImpl final : public FactorBase {
     if (!dry_run()) {
       if (inv_.b.dev) dev_free(inv_.b.dev);
       if (fwd_.b.dev) dev_free(fwd_.b.dev);
+      for (Program<T>* P : {&inv_, &fwd_}) {
+        if (P->exec) cudaGraphExecDestroy(P->exec);
+        if (P->graph) cudaGraphDestroy(P->graph);
+        P->exec = nullptr;
+        P->graph = nullptr;
+      }
     }
     inv_.b.dev = fwd_.b.dev = nullptr;
   }
@@ -434,12 +506,93 @@ class FactorImpl final : public FactorBase {
   void run_program(Program<T>& P, const double* x, double* y, cudaStream_t s) {
     T* v1 = lev_.empty() ? vtop_ : vb_[0];
     launch_gather<T>(x, perm1_, v1, n, s);
-    for (auto& op : P.ops) op(P.b.dev, s);
+    if (dry_run()) {
+      for (auto& op : P.ops) op(P.b.dev, s);
+    } else {
+      if (!P.exec) capture(P);
+      SGF_CK(cudaGraphLaunch(P.exec, s));
+      for (const auto& a : P.acct) prof_count(a.kind, a.flops, a.bytes);
+    }
     launch_scatter<T>(v1, perm1_, y, n, s);
+  }
+
+  // record the program's launches once on a private stream
+  void capture(Program<T>& P) {
+    cudaStream_t cs;
+    SGF_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    prof_capture(true);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (auto& op : P.ops) op(P.b.dev, cs);
+      e = cudaStreamEndCapture(cs, &P.graph);
+    }
+    prof_capture(false);
+    cudaStreamDestroy(cs);
+    SGF_CK(e);
+    SGF_CK(cudaGraphInstantiate(&P.exec, P.graph, 0));
+  }
+
+  // device copies of the plan's constant data (assembly map, DOF order,
+  // level-1 bases, re-expansion matrices), uploaded once per plan and device
+  struct PlanData {
+    const int64_t* map;
+    const int64_t* perm;
+    const T* phi1;
+    std::vector<const T*> reexp;
+  };
+  static PlanData plan_data(const Plan& P, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(P.cache_mu);
+    Plan::DevCache& C = P.cache;
+    int dev = 0;
+    if (!dry_run()) SGF_CK(cudaGetDevice(&dev));
+    if (C.device >= 0 && C.device != dev)
+      throw SgfError(SGF_ERR_INVALID_ARG, "plan data cached on another device");
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (!C.map) {
+      C.device = dev;
+      C.map = (int64_t*)dev_malloc(std::max<size_t>(P.asm_map.size(), 1) * 8);
+      dev_h2d(C.map, P.asm_map.data(), P.asm_map.size() * 8, s);
+      C.perm = (int64_t*)dev_malloc(std::max<size_t>(P.perm1.size(), 1) * 8);
+      dev_h2d(C.perm, P.perm1.data(), P.perm1.size() * 8, s);
+    }
+    if (!C.phi1[ti]) {
+      std::vector<T> h(P.phi1.size());
+      for (size_t i = 0; i < h.size(); ++i) h[i] = (T)P.phi1[i];
+      C.phi1[ti] = dev_malloc(std::max<size_t>(h.size(), 1) * sizeof(T));
+      dev_h2d(C.phi1[ti], h.data(), h.size() * sizeof(T), s);
+      C.reexp[ti].assign(P.lev.size(), nullptr);
+      for (size_t li = 1; li < P.lev.size(); ++li) {
+        const auto& r = P.lev[li].reexp;
+        std::vector<T> hr(r.size());
+        for (size_t i = 0; i < hr.size(); ++i) hr[i] = (T)r[i];
+        C.reexp[ti][li] = dev_malloc(std::max<size_t>(hr.size(), 1) * sizeof(T));
+        dev_h2d(C.reexp[ti][li], hr.data(), hr.size() * sizeof(T), s);
+      }
+      dev_sync(s);
+    }
+    PlanData d;
+    d.map = C.map;
+    d.perm = C.perm;
+    d.phi1 = (const T*)C.phi1[ti];
+    for (void* p : C.reexp[ti]) d.reexp.push_back((const T*)p);
+    return d;
+  }
+
+  // SGF_TRACE=1: synchronize and print the wall time of each factor phase
+  bool trace_on_ = std::getenv("SGF_TRACE") != nullptr;
+  std::chrono::steady_clock::time_point trace_t0_ = std::chrono::steady_clock::now();
+  void trace(cudaStream_t s, int level, const char* what) {
+    if (!trace_on_) return;
+    if (!dry_run()) cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[sgf trace] level %d %-22s %8.3f ms\n", level, what,
+                 std::chrono::duration<double, std::milli>(now - trace_t0_).count());
+    trace_t0_ = now;
   }
 
   void build(const double* coeffs, cudaStream_t s) {
     const Plan& P = *plan;
+    trace(s, 0, "start");
     const int pi = P.pi;
     Batch b;
     // ---- level 1 sizes, layout, assembly --------------------------------
@@ -454,60 +607,20 @@ class FactorImpl final : public FactorBase {
     sx_ = dalloc<double>(keep_, P.npts, s);
     sy_ = dalloc<double>(keep_, P.npts, s);
     sz_ = dalloc<double>(keep_, P.npts, s);
+    const PlanData pd = plan_data(P, s);
+    perm1_ = pd.perm;
     {
-      std::vector<int> node_of(P.npts), lpos(P.npts);
-      std::vector<int64_t> perm(P.npts);
-      for (int u = 0; u < L1.nnodes; ++u)
-        for (int k = L1.pt_ptr[u]; k < L1.pt_ptr[u + 1]; ++k) {
-          const int p = L1.pt_idx[k];
-          node_of[p] = u;
-          lpos[p] = k - L1.pt_ptr[u];
-          perm[lay.vec_off[u] + lpos[p]] = p;
-        }
-      std::vector<int64_t> map(P.npts * 7, -1);
-      const int64_t nxy = (int64_t)P.nx * P.ny;
-      for (int64_t p = 0; p < P.npts; ++p) {
-        const int x = (int)(p % P.nx), y = (int)((p / P.nx) % P.ny), z = (int)(p / nxy);
-        const int u = node_of[p], lp = lpos[p];
-        const int64_t nbq[6] = {x > 0 ? p - 1 : -1, x < P.nx - 1 ? p + 1 : -1,
-                                y > 0 ? p - P.nx : -1, y < P.ny - 1 ? p + P.nx : -1,
-                                z > 0 ? p - nxy : -1, z < P.nz - 1 ? p + nxy : -1};
-        for (int q = 0; q < 6; ++q) {
-          if (nbq[q] < 0) continue;
-          const int v = node_of[nbq[q]], lq = lpos[nbq[q]];
-          if (u == v) map[p * 7 + q] = lay.dg_off[u] + lp + (int64_t)lq * m[u];
-          else if (u < v) {
-            const int col = lay.col_of(u, v);
-            if (col < 0) throw SgfError(SGF_ERR_CUDA, "internal: missing level-1 block");
-            map[p * 7 + q] = lay.dg_size + lay.up_off[u] + (int64_t)(col + lq) * m[u] + lp;
-          }
-        }
-        map[p * 7 + 6] = lay.dg_off[u] + lp + (int64_t)lp * m[u];
-      }
-      if (dry_run())
-        for (int64_t v : map)
-          if (v >= lay.dg_size + lay.up_size) check_range(nullptr, 1, "assembly map entry out of range");
-      int64_t* dmap = walloc<int64_t>(work_, map.size(), s, false);
-      dev_h2d(dmap, map.data(), map.size() * 8, s);
-      perm1_ = dalloc<int64_t>(keep_, P.npts, s, false);
-      dev_h2d(perm1_, perm.data(), perm.size() * 8, s);
       const double w = P.stencil == SGF_STENCIL_7PT_FV_3D ? 2.0 : 1.0;
-      launch_assemble_scalar<T>(coeffs, P.nx, P.ny, P.nz, P.grid.dirichlet, w, dmap, lay.dg_size, Dg, Up,
+      launch_assemble_scalar<T>(coeffs, P.nx, P.ny, P.nz, P.grid.dirichlet, w, pd.map, lay.dg_size, Dg, Up,
                                 sd_, sx_, sy_, sz_, s);
       if (!dry_run()) SGF_CK(cudaGetLastError());
-      dev_sync(s);
-      free_work(s);
     }
-    // level-1 Phi
+    trace(s, 1, "assembly");
+    // level-1 Phi: a working copy (merges write the next level's)
     T* Phi = nullptr;
     std::vector<void*> phiw;
-    {
-      std::vector<T> h(P.phi1.size());
-      for (size_t i = 0; i < h.size(); ++i) h[i] = (T)P.phi1[i];
-      Phi = walloc<T>(phiw, std::max<size_t>(h.size(), 1), s, false);
-      dev_h2d(Phi, h.data(), h.size() * sizeof(T), s);
-      dev_sync(s);
-    }
+    Phi = walloc<T>(phiw, std::max<size_t>(P.phi1.size(), 1), s, false);
+    dev_d2d(Phi, pd.phi1, P.phi1.size() * sizeof(T), s);
 
     for (size_t li = 0; li < P.lev.size(); ++li) {
       const LevelSym& L = P.lev[li];
@@ -521,6 +634,7 @@ class FactorImpl final : public FactorBase {
         Litop_ = dalloc<T>(keep_, (size_t)mtop_ * mtop_, s);
         std::vector<Front<T>> F = {{Dg, mtop_, nullptr, 0, Litop_, 0}};
         if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl);
+        b.run(s);
         check_status(s);
         ls.size_before = ls.size_after = mtop_;
         ls.bytes = (int64_t)2 * mtop_ * mtop_ * sizeof(T);
@@ -537,21 +651,35 @@ class FactorImpl final : public FactorBase {
       for (int i = 0; i < nn; ++i)
         if (L.interior[i] && m[i] > 0) { li_off[i] = li_tot; li_tot += (int64_t)m[i] * m[i]; }
       T* LiI = dalloc<T>(keep_, li_tot, s);
+      int64_t w_tot = 0;
+      std::vector<int64_t> w_off(nn, -1);
+      for (int i = 0; i < nn; ++i)
+        if (L.interior[i] && m[i] > 0) { w_off[i] = w_tot; w_tot += (int64_t)m[i] * lay.up_w[i]; }
+      T* Wb = dalloc<T>(keep_, w_tot, s, false);
       std::vector<Front<T>> F;
       for (int i = 0; i < nn; ++i) {
         if (!L.interior[i] || m[i] == 0) continue;
-        F.push_back({Dg + lay.dg_off[i], m[i], Up + lay.up_off[i], lay.up_w[i], LiI + li_off[i], i});
+        F.push_back({Dg + lay.dg_off[i], m[i], nullptr, 0, LiI + li_off[i], i});
         InteriorRec<T> r;
         r.node = i;
         r.m = m[i];
         r.s = lay.up_w[i];
         r.L = Dg + lay.dg_off[i];
         r.Li = LiI + li_off[i];
-        r.W = Up + lay.up_off[i];
+        r.W = Wb + w_off[i];
         for (int k = lay.up_ptr[i]; k < lay.up_ptr[i + 1]; ++k) r.nb.push_back({lay.up_nb[k], lay.up_col[k]});
         rec.in.push_back(r);
       }
       run_fronts<T>(F, b, s, st_, lvl);
+      b.run(s);
+      trace(s, lvl, "interior fronts");
+      {
+        // W_I = L_I^{-1} A_I,S (Sec. 4.1), one launch over all interiors
+        GemmList<T> gw;
+        for (const auto& r : rec.in)
+          if (r.s > 0) gw.add_lowtri(r.W, r.m, r.m, r.s, r.Li, r.m, Up + lay.up_off[r.node], r.m);
+        gw.emit(b, s);
+      }
       {
         // Schur complement, owner-computes per target block
         std::map<T*, std::pair<std::array<int, 3>, std::vector<Spec<T>>>> tg;
@@ -577,6 +705,7 @@ class FactorImpl final : public FactorBase {
         gl.emit(b, s);
         b.run(s);
       }
+      trace(s, lvl, "W + Schur");
       // ---------------- 2. compression, phase 1 --------------------------
       std::vector<std::vector<int>> nball(nn);
       for (size_t p = 0; p < L.post.size(); p += 2) {
@@ -608,12 +737,13 @@ class FactorImpl final : public FactorBase {
         max_m = std::max(max_m, m[B]);
         max_c = std::max(max_c, cw[e]);
       }
-      if (max_c + std::min(max_m, max_c) + max_m > 24000)
+      if (qr_smem_bytes(max_m, max_c, sizeof(T), 0) > 220 * 1024)
         throw SgfError(SGF_ERR_UNSUPPORTED, "node too large for the QR kernel");
       T* Dw = dalloc<T>(keep_, t_mm, s, false);
       T* LiB = dalloc<T>(keep_, t_mm, s);
       T* Q1 = dalloc<T>(keep_, t_mm, s, false);
       T* G = walloc<T>(work_, t_ms, s, false);
+      T* Mh = walloc<T>(work_, t_ms, s, false);
       T* Nm = walloc<T>(work_, t_mc, s, false);
       T* LtP = walloc<T>(work_, t_mp, s, false);
       int* dranks = walloc<int>(work_, ne, s);
@@ -638,8 +768,15 @@ class FactorImpl final : public FactorBase {
       }
       {
         std::vector<Front<T>> FB;
-        for (int e = 0; e < ne; ++e) FB.push_back({Dw + o_mm[e], m[E[e]], G + o_ms[e], sw[e], LiB + o_mm[e], E[e]});
+        for (int e = 0; e < ne; ++e) FB.push_back({Dw + o_mm[e], m[E[e]], nullptr, 0, LiB + o_mm[e], E[e]});
         run_fronts<T>(FB, b, s, st_, lvl);
+        {
+          // M^_B,nbrs = L_B^{-1} A_B,nbrs (Eq. (compr-scale))
+          GemmList<T> gm;
+          for (int e = 0; e < ne; ++e)
+            if (sw[e] > 0) gm.add_lowtri(Mh + o_ms[e], m[E[e]], m[E[e]], sw[e], LiB + o_mm[e], m[E[e]], G + o_ms[e], m[E[e]]);
+          gm.emit(b, s);
+        }
         CopyList<T, T> cz;
         for (int e = 0; e < ne; ++e) {
           const int mb = m[E[e]];
@@ -655,7 +792,7 @@ class FactorImpl final : public FactorBase {
           int j = 1;
           for (int N : nball[B]) {
             gl.add(Nb + (size_t)j * pi * mb, mb, mb, pi, T(1), 0,
-                   {{G + o_ms[e] + (size_t)gcol[e][N] * mb, mb, false, Phi + lay.vec_off[N] * pi, m[N], false, m[N]}});
+                   {{Mh + o_ms[e] + (size_t)gcol[e][N] * mb, mb, false, Phi + lay.vec_off[N] * pi, m[N], false, m[N]}});
             ++j;
           }
         }
@@ -664,20 +801,48 @@ class FactorImpl final : public FactorBase {
         CopyList<T, T> cp;
         for (int e = 0; e < ne; ++e) cp.add(Nm + o_mc[e], m[E[e]], LtP + o_mp[e], m[E[e]], m[E[e]], pi, kCopy);
         cp.emit(b, s);
-        std::vector<QrTask<T>> qt;
-        for (int e = 0; e < ne; ++e) qt.push_back({Nm + o_mc[e], Q1 + o_mm[e], m[E[e]], cw[e], E[e], 0});
-        if (!qt.empty()) {
-          const size_t oq = b.push(qt);
-          const int nq = (int)qt.size();
-          const double tau = P.tau;
-          DevStatus* st = st_;
+        // shared-memory sweep when m x (columns not identically zero) fits
+        std::vector<QrTask<T>> qs, qg;
+        int sm_m = 1, sm_c = 1, g_m = 1, g_c = 1;
+        long long cap = 0;
+        const size_t budget = 200 * 1024;
+        for (int e = 0; e < ne; ++e) {
+          const int B = E[e];
+          int ce = L.act[B];
+          for (int N : nball[B]) ce += L.act[N];
+          ce = std::min(ce, cw[e]);
+          QrTask<T> q{Nm + o_mc[e], Q1 + o_mm[e], m[B], cw[e], B, e};
+          const long long need = (long long)m[B] * ce;
+          if (qr_smem_bytes(std::max(sm_m, m[B]), std::max(sm_c, cw[e]), sizeof(T), std::max(cap, need)) <= budget) {
+            qs.push_back(q);
+            sm_m = std::max(sm_m, m[B]);
+            sm_c = std::max(sm_c, cw[e]);
+            cap = std::max(cap, need);
+          } else {
+            qg.push_back(q);
+            g_m = std::max(g_m, m[B]);
+            g_c = std::max(g_c, cw[e]);
+          }
+        }
+        const double tau = P.tau;
+        for (int pass = 0; pass < 2; ++pass) {
+          auto& q = pass == 0 ? qs : qg;
+          if (q.empty()) continue;
+          double fl = 0;
+          for (const auto& t : q) fl += 4.0 * t.m * t.c * std::min(t.m, t.c);
+          const size_t oq = b.push(q);
+          const int nq = (int)q.size();
+          const int mm = pass == 0 ? sm_m : g_m, mc = pass == 0 ? sm_c : g_c;
+          const long long cp = pass == 0 ? cap : 0;
           b.launches.push_back([=](const char* d) {
-            launch_qrcp<T>((const QrTask<T>*)(d + oq), nq, dranks, tau, max_m, max_c, st, lvl, s);
+            prof_work(fl, 0);
+            launch_qrcp<T>((const QrTask<T>*)(d + oq), nq, dranks, tau, mm, mc, cp, s);
           });
         }
         b.run(s);
       }
       check_status(s);
+      trace(s, lvl, "compression to QR");
       std::vector<int> rk(ne, 0);
       if (ne) dev_d2h(rk.data(), dranks, ne * sizeof(int), s);
       if (dry_run())  // a deterministic stand-in that exercises both outcomes
@@ -755,13 +920,13 @@ class FactorImpl final : public FactorBase {
           T* K = Kb + ko[q];
           if (comp[C] && !comp[Cp]) {
             g1.add(K, kk[C], kk[C], m[Cp], T(1), 0,
-                   {{Q1 + o_mm[e], m[C], true, G + o_ms[e] + (size_t)gcol[e][Cp] * m[C], m[C], false, m[C]}});
+                   {{Q1 + o_mm[e], m[C], true, Mh + o_ms[e] + (size_t)gcol[e][Cp] * m[C], m[C], false, m[C]}});
           } else if (!comp[C] && comp[Cp]) {
             g1.add(K, m[C], m[C], kk[Cp], T(1), 0, {{X, m[C], false, Yh + o_mr[ep], m[Cp], false, m[Cp]}});
           } else {
             T* T1q = T1 + to[q];
             g1.add(T1q, m[C], m[C], kk[Cp], T(1), 0,
-                   {{G + o_ms[e] + (size_t)gcol[e][Cp] * m[C], m[C], false, Yh + o_mr[ep], m[Cp], false, m[Cp]}});
+                   {{Mh + o_ms[e] + (size_t)gcol[e][Cp] * m[C], m[C], false, Yh + o_mr[ep], m[Cp], false, m[Cp]}});
             g2.add(K, kk[C], kk[C], kk[Cp], T(1), 0, {{Q1 + o_mm[e], m[C], true, T1q, m[C], false, m[C]}});
           }
           src[q] = {K, kk[C]};
@@ -772,10 +937,7 @@ class FactorImpl final : public FactorBase {
       }
       // ---------------- 4. merge into the next level --------------------
       {
-        std::vector<T> hr(Ln.reexp.size());
-        for (size_t i = 0; i < hr.size(); ++i) hr[i] = (T)Ln.reexp[i];
-        T* R = walloc<T>(work_, std::max<size_t>(hr.size(), 1), s, false);
-        if (!hr.empty()) dev_h2d(R, hr.data(), hr.size() * sizeof(T), s);
+        const T* R = pd.reexp[li + 1];
         CopyList<T, T> cl;
         GemmList<T> gl;
         for (int C = 0; C < nn; ++C) {
@@ -811,6 +973,7 @@ class FactorImpl final : public FactorBase {
         gl.emit(b, s);
         b.run(s);
       }
+      trace(s, lvl, "two-sided + merge");
       // ---------------- records for the apply ----------------------------
       for (int C = 0; C < nn; ++C) {
         if (L.interior[C]) continue;
@@ -836,8 +999,7 @@ class FactorImpl final : public FactorBase {
       ls.bytes = bytes;
       stats.push_back(ls);
       lev_.push_back(std::move(rec));
-      dev_sync(s);
-      free_work(s);
+      free_work(s);   // stream ordered: the host goes on building level t+1
       for (void* p : phiw) dev_free_async(p, s);
       phiw = phin;
       Phi = Phin;
@@ -881,6 +1043,11 @@ class FactorImpl final : public FactorBase {
   }
 
   void veccopy(Program<T>& P, std::vector<VecCopyTask>& v, const T* src, T* dst) {
+    if (!v.empty()) {
+      double by = 0;
+      for (const auto& t : v) by += 2.0 * sizeof(T) * t.len;
+      P.acct.push_back({P_VECCOPY, 0.0, by});
+    }
     emit_veccopy_impl(v, P.b, P.ops, [src, dst](const VecCopyTask* t, int n, cudaStream_t s) {
       launch_veccopy<T>(t, n, src, dst, s);
     });

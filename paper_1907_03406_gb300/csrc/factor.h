@@ -34,8 +34,16 @@ struct Batch {
   std::vector<char> host;
   std::vector<char> keep_host;  // dry-run copy of a persistent program
   std::vector<std::function<void(const char*)>> launches;
-  char* dev = nullptr;
+  char* dev = nullptr;   // persistent programs only
   size_t cap = 0;
+  char* pin[2] = {nullptr, nullptr};
+  size_t pincap[2] = {0, 0};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int cur = 0;
+  Batch() = default;
+  Batch(const Batch&) = delete;
+  Batch& operator=(const Batch&) = delete;
+  ~Batch();
   template <class X>
   size_t push(const std::vector<X>& v) {
     size_t off = (host.size() + 63) & ~size_t(63);

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 
 #include "devmem.h"
 #include "kernels.h"
@@ -111,26 +112,123 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmTask<T>* __restrict
     }
 }
 
+
+// FP32 variant: each thread owns a 4x4 block of consecutive rows / columns so
+// every operand fetch from shared memory is one 16-byte load; the next K chunk
+// is prefetched into registers while the current one is multiplied.
+constexpr int kPitchF = kTile + 4;  // keeps 16-byte alignment, breaks bank aliasing
+
+__device__ __forceinline__ void gemm_load_chunk(const GemmContrib<float>& cb, int M, int N, int k0,
+                                                float ra[4], float rb[4]) {
+  const bool ta = cb.flags & kTransA, tb = cb.flags & kTransB;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + kThreads * q;
+    int i, kk;
+    if (!ta) { i = e & 63; kk = e >> 6; } else { kk = e & 15; i = e >> 4; }
+    float v = 0.f;
+    if (i < M && k0 + kk < cb.K)
+      v = ta ? cb.A[(size_t)(k0 + kk) + (size_t)i * cb.lda] : cb.A[(size_t)i + (size_t)(k0 + kk) * cb.lda];
+    ra[q] = v;
+    int j;
+    if (!tb) { kk = e & 15; j = e >> 4; } else { j = e & 63; kk = e >> 6; }
+    v = 0.f;
+    if (j < N && k0 + kk < cb.K)
+      v = tb ? cb.B[(size_t)j + (size_t)(k0 + kk) * cb.ldb] : cb.B[(size_t)(k0 + kk) + (size_t)j * cb.ldb];
+    rb[q] = v;
+  }
+}
+
+__device__ __forceinline__ void gemm_store_chunk(const GemmContrib<float>& cb, float (*As)[kPitchF],
+                                                 float (*Bs)[kPitchF], const float ra[4], const float rb[4]) {
+  const bool ta = cb.flags & kTransA, tb = cb.flags & kTransB;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + kThreads * q;
+    int i, kk;
+    if (!ta) { i = e & 63; kk = e >> 6; } else { kk = e & 15; i = e >> 4; }
+    As[kk][i] = ra[q];
+    int j;
+    if (!tb) { kk = e & 15; j = e >> 4; } else { j = e & 63; kk = e >> 6; }
+    Bs[kk][j] = rb[q];
+  }
+}
+
+template <>
+__global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>* __restrict__ tasks,
+                                                          const GemmContrib<float>* __restrict__ cons) {
+  const GemmTask<float> tk = tasks[blockIdx.x];
+  __shared__ __align__(16) float As[2][kKC][kPitchF];
+  __shared__ __align__(16) float Bs[2][kKC][kPitchF];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+  for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
+    const GemmContrib<float> cb = cons[c];
+    float ra[4], rb[4];
+    gemm_load_chunk(cb, tk.M, tk.N, 0, ra, rb);
+    __syncthreads();  // previous contribution done with the buffers
+    gemm_store_chunk(cb, As[0], Bs[0], ra, rb);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < cb.K; k0 += kKC) {
+      const bool more = k0 + kKC < cb.K;
+      if (more) gemm_load_chunk(cb, tk.M, tk.N, k0 + kKC, ra, rb);
+#pragma unroll
+      for (int kk = 0; kk < kKC; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+      }
+      if (more) {
+        gemm_store_chunk(cb, As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = ty * 4 + r;
+    if (i >= tk.M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = tx * 4 + q;
+      if (j < tk.N) {
+        float* p = tk.C + (size_t)i + (size_t)j * tk.ldc;
+        float v = tk.alpha * acc[r][q];
+        if (tk.beta) v += *p;
+        *p = v;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // diagonal tile: Cholesky + inverse of the factor
 // ---------------------------------------------------------------------------
 constexpr int kPitch = kTile + 1;
 
+// Cholesky of the n x n tile A (ld lda) in shared memory S, L^{-1} in V;
+// writes L (strict upper part zeroed) back to A and L^{-1} to Li.  Returns
+// 0, 1 (pivot <= 0) or 2 (non-finite pivot), the same in every thread.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_diag(const DiagTask<T>* __restrict__ tasks,
-                                                   DevStatus* st, int level) {
-  const DiagTask<T> tk = tasks[blockIdx.x];
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* S = reinterpret_cast<T*>(smraw);
-  T* V = S + kTile * kPitch;
+__device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
   __shared__ int bad;
-  const int n = tk.n;
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
     const int i = e % n, j = e / n;
-    S[i * kPitch + j] = tk.A[(size_t)i + (size_t)j * tk.lda];
+    S[i * kPitch + j] = A[(size_t)i + (size_t)j * lda];
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
       T d = S[j * kPitch + j];
@@ -144,26 +242,146 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagTask<T>* __restrict
     const T dj = S[j * kPitch + j];
     for (int i = j + 1 + threadIdx.x; i < n; i += kThreads) S[i * kPitch + j] /= dj;
     __syncthreads();
-    const int w = n - j - 1;
-    for (int p = threadIdx.x; p < w * w; p += kThreads) {
-      const int i = j + 1 + p / w, k = j + 1 + p % w;
-      if (k <= i) S[i * kPitch + k] -= S[i * kPitch + j] * S[k * kPitch + j];
+    // trailing lower triangle, 16 x 16 thread grid
+    for (int i = j + 1 + ty; i < n; i += 16) {
+      const T lij = S[i * kPitch + j];
+      for (int k = j + 1 + tx; k <= i; k += 16) S[i * kPitch + k] -= lij * S[k * kPitch + j];
     }
     __syncthreads();
   }
-  // V = L^{-1}, row by row (row i needs rows < i)
-  for (int i = 0; i < n; ++i) {
-    for (int c = threadIdx.x; c <= i; c += kThreads) {
-      T s = (c == i) ? T(1) : T(0);
-      for (int k = c; k < i; ++k) s -= S[i * kPitch + k] * V[k * kPitch + c];
-      V[i * kPitch + c] = s / S[i * kPitch + i];
+  // V = L^{-1} row by row; each entry V[i][c] is a dot product split over 4
+  // neighbouring lanes
+  {
+    const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
+    for (int i = 0; i < n; ++i) {
+      T sum = T(0);
+      if (c < i)
+        for (int k = c + part; k < i; k += 4) sum = fma(S[i * kPitch + k], V[k * kPitch + c], sum);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      if (part == 0 && c <= i) V[i * kPitch + c] = ((c == i ? T(1) : T(0)) - sum) / S[i * kPitch + i];
+      __syncthreads();
     }
-    __syncthreads();
   }
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
     const int i = e % n, j = e / n;
-    tk.A[(size_t)i + (size_t)j * tk.lda] = (i >= j) ? S[i * kPitch + j] : T(0);
-    tk.Li[(size_t)i + (size_t)j * tk.ldli] = (i >= j) ? V[i * kPitch + j] : T(0);
+    A[(size_t)i + (size_t)j * lda] = (i >= j) ? S[i * kPitch + j] : T(0);
+    Li[(size_t)i + (size_t)j * ldli] = (i >= j) ? V[i * kPitch + j] : T(0);
+  }
+  __syncthreads();
+  return bad;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_diag(const DiagTask<T>* __restrict__ tasks,
+                                                   DevStatus* st, int level) {
+  const DiagTask<T> tk = tasks[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* S = reinterpret_cast<T*>(smraw);
+  T* V = S + kTile * kPitch;
+  const int bad = diag_tile<T>(tk.A, tk.lda, tk.Li, tk.ldli, tk.n, S, V);
+  if (threadIdx.x == 0 && bad) report(st, bad == 1 ? SGF_ERR_NOT_SPD : SGF_ERR_NONFINITE, level, tk.node);
+}
+
+// C[M x N] = beta C + alpha op(A) op(B), M, N <= 64, by the whole CTA, with
+// shared staging As/Bs (kKC x (kTile + 1) each).  Ends with a barrier.
+template <typename T>
+__device__ void cta_gemm(T* C, int ldc, int M, int N, T alpha, int beta, const T* A, int lda, bool ta,
+                         const T* B, int ldb, bool tb, int K, T (*As)[kTile + 1], T (*Bs)[kTile + 1]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
+  for (int k0 = 0; k0 < K; k0 += kKC) {
+#pragma unroll
+    for (int q = 0; q < (kKC * kTile) / kThreads; ++q) {
+      const int e = threadIdx.x + kThreads * q;
+      int i, kk;
+      if (!ta) { i = e & 63; kk = e >> 6; } else { kk = e & 15; i = e >> 4; }
+      T v = T(0);
+      if (i < M && k0 + kk < K)
+        v = ta ? A[(size_t)(k0 + kk) + (size_t)i * lda] : A[(size_t)i + (size_t)(k0 + kk) * lda];
+      As[kk][i] = v;
+      int j;
+      if (!tb) { kk = e & 15; j = e >> 4; } else { j = e & 63; kk = e >> 6; }
+      v = T(0);
+      if (j < N && k0 + kk < K)
+        v = tb ? B[(size_t)j + (size_t)(k0 + kk) * ldb] : B[(size_t)(k0 + kk) + (size_t)j * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKC; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        a[r] = As[kk][ty + 16 * r];
+        b[r] = Bs[kk][tx + 16 * r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ty + 16 * r, j = tx + 16 * q;
+      if (i < M && j < N) {
+        T* p = C + (size_t)i + (size_t)j * ldc;
+        T v = alpha * acc[r][q];
+        if (beta) v += *p;
+        *p = v;
+      }
+    }
+  __syncthreads();
+}
+
+// Whole blocked Cholesky of an m x m front D with L^{-1} in Li, one CTA per
+// front (small fronts): the same diagonal-tile / panel / trailing-update
+// sweep as the multi-launch path, without a launch per step.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_front(const FrontTask<T>* __restrict__ tasks,
+                                                    DevStatus* st, int level) {
+  const FrontTask<T> tk = tasks[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* S = reinterpret_cast<T*>(smraw);
+  T* V = S + kTile * kPitch;
+  T (*As)[kTile + 1] = reinterpret_cast<T (*)[kTile + 1]>(V + kTile * kPitch);
+  T (*Bs)[kTile + 1] = As + kKC;
+  const int m = tk.m;
+  T* D = tk.D;
+  T* Li = tk.Li;
+  const int nt = (m + kTile - 1) / kTile;
+  int bad = 0;
+  for (int k = 0; k < nt; ++k) {
+    const int r0 = k * kTile, nk = min(kTile, m - r0), r1 = r0 + nk;
+    T* Likk = Li + r0 + (size_t)r0 * m;
+    const int b = diag_tile<T>(D + r0 + (size_t)r0 * m, m, Likk, m, nk, S, V);
+    if (b && !bad) bad = b;
+    for (int ri = r1; ri < m; ri += kTile) {
+      T* C = D + ri + (size_t)r0 * m;
+      cta_gemm<T>(C, m, min(kTile, m - ri), nk, T(1), 0, C, m, false, Likk, m, true, nk, As, Bs);
+    }
+    for (int j0 = 0; j0 < r0; j0 += kTile) {
+      T* C = Li + r0 + (size_t)j0 * m;
+      cta_gemm<T>(C, m, nk, min(kTile, r0 - j0), T(1), 0, Likk, m, false, C, m, false, nk, As, Bs);
+    }
+    for (int rj = r1; rj < m; rj += kTile) {
+      const int nj = min(kTile, m - rj);
+      for (int ri = rj; ri < m; ri += kTile)
+        cta_gemm<T>(D + ri + (size_t)rj * m, m, min(kTile, m - ri), nj, T(-1), 1, D + ri + (size_t)r0 * m, m,
+                    false, D + rj + (size_t)r0 * m, m, true, nk, As, Bs);
+    }
+    for (int ri = r1; ri < m; ri += kTile)
+      for (int j0 = 0; j0 < r1; j0 += kTile)
+        cta_gemm<T>(Li + ri + (size_t)j0 * m, m, min(kTile, m - ri), min(kTile, r1 - j0), T(-1), 1,
+                    D + ri + (size_t)r0 * m, m, false, Li + r0 + (size_t)j0 * m, m, false, nk, As, Bs);
   }
   if (threadIdx.x == 0 && bad) report(st, bad == 1 ? SGF_ERR_NOT_SPD : SGF_ERR_NONFINITE, level, tk.node);
 }
@@ -192,89 +410,108 @@ __global__ void __launch_bounds__(kThreads) k_copy(const CopyTask<S, D>* __restr
 // ---------------------------------------------------------------------------
 // column-pivoted Householder QR, rank and Q1 (one CTA per node)
 // ---------------------------------------------------------------------------
+// Columns that are exactly zero (monomials on the flat axes of a face or edge
+// cell, Sec. 3.1) are dropped before the sweep; pivoting swaps entries of a
+// column map instead of moving data; the pivot of step k is the largest of
+// the per-warp maxima recorded while step k-1 refreshed the trailing column
+// norms.  The matrix is copied to shared memory when m * c_eff fits in the
+// launch's capacity, else the sweep runs on the global workspace.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_qrcp(const QrTask<T>* __restrict__ tasks, int* ranks,
-                                                   double tau, DevStatus* st, int level) {
+                                                   double tau, long long cap_elems) {
+  using Acc = T;  // column sweeps in the working precision (FP64 is ~1/64 rate here)
   const QrTask<T> tk = tasks[blockIdx.x];
   const int m = tk.m, c = tk.c;
+  const int kmn = m < c ? m : c;
   extern __shared__ __align__(16) unsigned char smraw[];
   double* norms = reinterpret_cast<double*>(smraw);   // c
-  double* betas = norms + c;                          // min(m, c)
-  T* v = reinterpret_cast<T*>(betas + (m < c ? m : c));  // m
-  __shared__ double rv[32];
-  __shared__ int ri[32];
-  __shared__ double s_bcast;
-  __shared__ int s_piv;
+  double* betas = norms + c;                          // kmn
+  int* colmap = reinterpret_cast<int*>(betas + kmn);  // c
+  uintptr_t vp = (reinterpret_cast<uintptr_t>(colmap + c) + 15) & ~uintptr_t(15);
+  T* v = reinterpret_cast<T*>(vp);                    // m
+  uintptr_t mp = (reinterpret_cast<uintptr_t>(v + m) + 15) & ~uintptr_t(15);
+  T* Ms = reinterpret_cast<T*>(mp);                   // cap_elems
+  __shared__ double pv[kThreads / 32];
+  __shared__ int pj[kThreads / 32];
+  __shared__ double s_x;
+  __shared__ int s_i;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
   T* A = tk.A;
   for (int j = warp; j < c; j += nw) {
-    double s = 0;
+    Acc sq = 0;
     for (int i = lane; i < m; i += 32) {
-      const double a = (double)A[(size_t)i + (size_t)j * m];
-      s += a * a;
+      const Acc a = A[(size_t)i + (size_t)j * m];
+      sq = fma(a, a, sq);
     }
-    s = warp_sum(s);
-    if (lane == 0) norms[j] = s;
+    sq = warp_sum(sq);
+    if (lane == 0) norms[j] = (double)sq;
   }
   __syncthreads();
-  const int kmax = m < c ? m : c;
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int j = 0; j < c; ++j)
+      if (norms[j] > 0.0) {
+        norms[cnt] = norms[j];
+        colmap[cnt] = j;
+        ++cnt;
+      }
+    s_i = cnt;
+  }
+  __syncthreads();
+  const int ce = s_i;
+  const bool in_smem = (long long)m * ce <= cap_elems;
+  T* M = A;
+  if (in_smem) {
+    for (int q = warp; q < ce; q += nw) {
+      const T* src = A + (size_t)colmap[q] * m;
+      for (int i = lane; i < m; i += 32) Ms[(size_t)i + (size_t)q * m] = src[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < ce; q += kThreads) colmap[q] = q;
+    M = Ms;
+  }
+  // initial per-warp maxima over all columns
+  {
+    double best = -1.0;
+    int bj = 1 << 30;
+    for (int j = warp; j < ce; j += nw)
+      if (norms[j] > best) { best = norms[j]; bj = j; }
+    if (lane == 0) { pv[warp] = best; pj[warp] = bj; }
+  }
+  __syncthreads();
+  const int kmax = m < ce ? m : ce;
   int r = 0;
   double ref = 0;
   for (int k = 0; k < kmax; ++k) {
-    // pivot: largest remaining column norm, lowest index on ties
-    double best = -1.0;
-    int bi = c;
-    for (int j = k + threadIdx.x; j < c; j += kThreads) {
-      const double x = norms[j];
-      if (x > best || (x == best && j < bi)) { best = x; bi = j; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
-    __syncthreads();
     if (threadIdx.x == 0) {
-      double b = rv[0];
-      int p = ri[0];
+      double b = pv[0];
+      int p = pj[0];
       for (int w = 1; w < nw; ++w)
-        if (rv[w] > b || (rv[w] == b && ri[w] < p)) { b = rv[w]; p = ri[w]; }
-      s_bcast = b;
-      s_piv = p;
+        if (pv[w] > b || (pv[w] == b && pj[w] < p)) { b = pv[w]; p = pj[w]; }
+      s_x = b;
+      s_i = p;
+      if (p != k && p < ce) {
+        const int t = colmap[k]; colmap[k] = colmap[p]; colmap[p] = t;
+        const double u = norms[k]; norms[k] = norms[p]; norms[p] = u;
+      }
     }
     __syncthreads();
-    const double nrm = sqrt(s_bcast > 0 ? s_bcast : 0.0);
-    const int p = s_piv;
+    const double nrm = sqrt(s_x > 0 ? s_x : 0.0);
     if (k == 0) ref = nrm;
     if (!(nrm > tau * ref) || ref == 0.0) break;
-    if (p != k) {
-      for (int i = threadIdx.x; i < m; i += kThreads) {
-        const T a = A[(size_t)i + (size_t)k * m];
-        A[(size_t)i + (size_t)k * m] = A[(size_t)i + (size_t)p * m];
-        A[(size_t)i + (size_t)p * m] = a;
-      }
-      if (threadIdx.x == 0) {
-        const double t = norms[k];
-        norms[k] = norms[p];
-        norms[p] = t;
-      }
-    }
-    __syncthreads();
-    // Householder vector of A[k:m, k]
-    double s = 0;
+    T* col = M + (size_t)colmap[k] * m;
+    Acc sq = 0;
     for (int i = k + threadIdx.x; i < m; i += kThreads) {
-      const T a = A[(size_t)i + (size_t)k * m];
+      const T a = col[i];
       v[i] = a;
-      s += (double)a * (double)a;
+      sq = fma(a, a, sq);
     }
-    s = warp_sum(s);
-    if (lane == 0) rv[warp] = s;
+    sq = warp_sum(sq);
+    if (lane == 0) pv[warp] = (double)sq;
     __syncthreads();
     if (threadIdx.x == 0) {
       double tot = 0;
-      for (int w = 0; w < nw; ++w) tot += rv[w];
+      for (int w = 0; w < nw; ++w) tot += pv[w];
       const double normx = sqrt(tot);
       const double x0 = (double)v[k];
       const double alpha = x0 >= 0 ? -normx : normx;
@@ -284,31 +521,33 @@ __global__ void __launch_bounds__(kThreads) k_qrcp(const QrTask<T>* __restrict__
         v[k] = (T)(x0 - alpha);
       }
       betas[k] = beta;
-      A[(size_t)k + (size_t)k * m] = v[k];
+      col[k] = v[k];
     }
     __syncthreads();
-    for (int i = k + 1 + threadIdx.x; i < m; i += kThreads) A[(size_t)i + (size_t)k * m] = v[i];
     const double beta = betas[k];
-    // apply H = I - beta v v^T to the trailing columns and refresh their norms
-    for (int j = k + 1 + warp; j < c; j += nw) {
-      T* col = A + (size_t)j * m;
-      double w = 0;
-      for (int i = k + lane; i < m; i += 32) w += (double)v[i] * (double)col[i];
+    double best = -1.0;
+    int bj = 1 << 30;
+    for (int j = k + 1 + warp; j < ce; j += nw) {
+      T* cj = M + (size_t)colmap[j] * m;
+      Acc w = 0;
+      for (int i = k + lane; i < m; i += 32) w = fma(v[i], cj[i], w);
       w = warp_sum(w);
-      const double f = beta * w;
-      double s2 = 0;
+      const Acc f = (Acc)beta * w;
+      Acc s2 = 0;
       for (int i = k + lane; i < m; i += 32) {
-        const T a = (T)((double)col[i] - f * (double)v[i]);
-        col[i] = a;
-        if (i > k) s2 += (double)a * (double)a;
+        const T a = fma(-f, v[i], cj[i]);
+        cj[i] = a;
+        if (i > k) s2 = fma(a, a, s2);
       }
       s2 = warp_sum(s2);
-      if (lane == 0) norms[j] = s2;
+      if (lane == 0) norms[j] = (double)s2;
+      if ((double)s2 > best) { best = (double)s2; bj = j; }
     }
+    if (lane == 0) { pv[warp] = best; pj[warp] = bj; }
     __syncthreads();
     r = k + 1;
   }
-  if (threadIdx.x == 0) ranks[blockIdx.x] = r;
+  if (threadIdx.x == 0) ranks[tk.slot] = r;
   // Q1 = H_0 ... H_{r-1} [I_r; 0]
   T* Q = tk.Q1;
   for (int e = threadIdx.x; e < m * r; e += kThreads) {
@@ -317,21 +556,20 @@ __global__ void __launch_bounds__(kThreads) k_qrcp(const QrTask<T>* __restrict__
   }
   __syncthreads();
   for (int k = r - 1; k >= 0; --k) {
-    for (int i = k + threadIdx.x; i < m; i += kThreads) v[i] = A[(size_t)i + (size_t)k * m];
+    const T* col = M + (size_t)colmap[k] * m;
+    for (int i = k + threadIdx.x; i < m; i += kThreads) v[i] = col[i];
     __syncthreads();
     const double beta = betas[k];
     for (int j = k + warp; j < r; j += nw) {
-      T* col = Q + (size_t)j * m;
-      double w = 0;
-      for (int i = k + lane; i < m; i += 32) w += (double)v[i] * (double)col[i];
+      T* qc = Q + (size_t)j * m;
+      Acc w = 0;
+      for (int i = k + lane; i < m; i += 32) w = fma(v[i], qc[i], w);
       w = warp_sum(w);
-      const double f = beta * w;
-      for (int i = k + lane; i < m; i += 32) col[i] = (T)((double)col[i] - f * (double)v[i]);
+      const Acc f = (Acc)beta * w;
+      for (int i = k + lane; i < m; i += 32) qc[i] = fma(-f, v[i], qc[i]);
     }
     __syncthreads();
   }
-  (void)st;
-  (void)level;
 }
 
 // ---------------------------------------------------------------------------
@@ -567,6 +805,22 @@ void launch_diag(const DiagTask<T>* tasks, int n, DevStatus* st, int level, cuda
   k_diag<T><<<n, kThreads, sm, s>>>(tasks, st, level);
 }
 
+template <typename T>
+void launch_front(const FrontTask<T>* tasks, int n, DevStatus* st, int level, cudaStream_t s) {
+  if (dry_run()) {
+    for (int i = 0; i < n; ++i) {
+      check_block(tasks[i].D, tasks[i].m, tasks[i].m, tasks[i].m, sizeof(T), "front D");
+      check_block(tasks[i].Li, tasks[i].m, tasks[i].m, tasks[i].m, sizeof(T), "front Li");
+    }
+    return;
+  }
+  if (n <= 0) return;
+  const size_t sm = 2 * sizeof(T) * kTile * kPitch + 2 * sizeof(T) * kKC * (kTile + 1);
+  cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ProfScope ps(P_DIAG, s);
+  k_front<T><<<n, kThreads, sm, s>>>(tasks, st, level);
+}
+
 template <typename S, typename D>
 void launch_copy(const CopyTask<S, D>* tasks, int n, cudaStream_t s) {
   if (dry_run()) {
@@ -584,25 +838,29 @@ void launch_copy(const CopyTask<S, D>* tasks, int n, cudaStream_t s) {
   k_copy<S, D><<<n, kThreads, 0, s>>>(tasks);
 }
 
+size_t qr_smem_bytes(int m, int c, size_t es, long long cap_elems) {
+  const int kmn = m < c ? m : c;
+  return 8 * (size_t)(c + kmn) + 4 * (size_t)c + 16 + es * (size_t)m + 16 + es * (size_t)cap_elems + 64;
+}
+
 template <typename T>
 void launch_qrcp(const QrTask<T>* tasks, int n, int* ranks, double tau, int max_m, int max_c,
-                 DevStatus* st, int level, cudaStream_t s) {
+                 long long cap_elems, cudaStream_t s) {
   if (dry_run()) {
     for (int i = 0; i < n; ++i) {
       const QrTask<T>& t = tasks[i];
       if (t.m > max_m || t.c > max_c) check_range(nullptr, 1, "qr size above launch bound");
       check_block(t.A, t.m, t.c, t.m, sizeof(T), "qr A");
       check_block(t.Q1, t.m, t.m < t.c ? t.m : t.c, t.m, sizeof(T), "qr Q1");
+      check_range(ranks + t.slot, sizeof(int), "qr rank slot");
     }
-    check_range(ranks, sizeof(int) * n, "qr ranks");
     return;
   }
   if (n <= 0) return;
-  const int kmin = max_m < max_c ? max_m : max_c;
-  const size_t sm = sizeof(double) * (size_t)(max_c + kmin) + sizeof(T) * (size_t)max_m + 16;
+  const size_t sm = qr_smem_bytes(max_m, max_c, sizeof(T), cap_elems);
   cudaFuncSetAttribute(k_qrcp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ProfScope ps(P_QR, s);
-  k_qrcp<T><<<n, kThreads, sm, s>>>(tasks, ranks, tau, st, level);
+  k_qrcp<T><<<n, kThreads, sm, s>>>(tasks, ranks, tau, cap_elems);
 }
 
 template <typename T>
@@ -726,8 +984,9 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
 #define SGF_INST(T)                                                                              \
   template void launch_gemm<T>(const GemmTask<T>*, const GemmContrib<T>*, int, cudaStream_t);   \
   template void launch_diag<T>(const DiagTask<T>*, int, DevStatus*, int, cudaStream_t);         \
+  template void launch_front<T>(const FrontTask<T>*, int, DevStatus*, int, cudaStream_t);       \
   template void launch_copy<T, T>(const CopyTask<T, T>*, int, cudaStream_t);                    \
-  template void launch_qrcp<T>(const QrTask<T>*, int, int*, double, int, int, DevStatus*, int,  \
+  template void launch_qrcp<T>(const QrTask<T>*, int, int*, double, int, int, long long,        \
                                cudaStream_t);                                                    \
   template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, cudaStream_t); \
   template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, cudaStream_t); \

@@ -20,11 +20,17 @@ void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* contribs, int n
                  cudaStream_t s);
 template <typename T>
 void launch_diag(const DiagTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
+// whole blocked Cholesky + inverse of small fronts, one CTA each
+constexpr int kFrontSmall = 512;
+template <typename T>
+void launch_front(const FrontTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
 template <typename S, typename D>
 void launch_copy(const CopyTask<S, D>* tasks, int ntasks, cudaStream_t s);
+// pivoted QR: tasks whose m * c_eff fits in cap_elems work in shared memory
 template <typename T>
 void launch_qrcp(const QrTask<T>* tasks, int ntasks, int* ranks, double tau, int max_m, int max_c,
-                 DevStatus* st, int level, cudaStream_t s);
+                 long long cap_elems, cudaStream_t s);
+size_t qr_smem_bytes(int m, int c, size_t elem_size, long long cap_elems);
 template <typename T>
 void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks,
                    cudaStream_t s);

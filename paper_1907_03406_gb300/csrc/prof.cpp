@@ -23,6 +23,7 @@ struct State {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
 };
+thread_local bool t_capturing = false;
 State& st() {
   static State s;
   return s;
@@ -59,6 +60,10 @@ void prof_work(double flops, double bytes) {
 ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
   State& S = st();
   std::lock_guard<std::mutex> g(S.mu);
+  if (t_capturing) {
+    S.next_flops = S.next_bytes = 0;
+    return;
+  }
   Acc& a = S.acc[kind];
   a.launches++;
   a.flops += S.next_flops;
@@ -81,6 +86,16 @@ ProfScope::~ProfScope() {
   std::lock_guard<std::mutex> g(S.mu);
   if (slot_ < (int)S.pending.size()) cudaEventRecord(S.pending[slot_].b, s_);
 }
+
+void prof_count(int kind, double flops, double bytes) {
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  S.acc[kind].launches++;
+  S.acc[kind].flops += flops;
+  S.acc[kind].bytes += bytes;
+}
+
+void prof_capture(bool on) { t_capturing = on; }
 
 void prof_reset(int timing) {
   State& S = st();

@@ -27,6 +27,11 @@ class ProfScope {
   int slot_;
 };
 
+// one launch of a replayed graph node: counted, not timed
+void prof_count(int kind, double flops, double bytes);
+// while a stream capture records launches, they are neither counted nor timed
+void prof_capture(bool on);
+
 void prof_reset(int timing);
 int prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes);
 const char* prof_name(int kind);

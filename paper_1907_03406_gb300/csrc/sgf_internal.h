@@ -7,6 +7,7 @@
 #include <array>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,8 @@ struct LevelSym {
   std::vector<char> interior;  // per node
   std::vector<int> cell_dim;   // per node
   std::vector<int> box;        // 6 per node: lo x,y,z then hi x,y,z
+  std::vector<int> act;        // per node: basis columns not identically zero
+                               // (monomials free of the cell's flat axes)
   std::vector<char> eligible;  // per node: selected for compression
   std::vector<int> child_ptr;  // nnodes + 1 (levels > 1)
   std::vector<int> child_idx;  // previous-level node ids, canonical order
@@ -55,6 +58,22 @@ struct Plan {
   std::vector<int64_t> phi1_off;
   // structural upper bounds of node sizes per level (for the footprint)
   std::vector<std::vector<int>> mcap;
+  // level-1 assembly: per point 7 destinations (x-, x+, y-, y+, z-, z+, diag)
+  // in the concatenation [diagonal blocks | upper panels] of the level-1
+  // layout (-1 = not stored), and the natural DOF of each level-1 vector slot
+  std::vector<int64_t> asm_map, perm1;
+
+  // device copies of the plan's constant data, built on first use
+  struct DevCache {
+    int device = -1;
+    int64_t* map = nullptr;
+    int64_t* perm = nullptr;
+    void* phi1[2] = {nullptr, nullptr};          // [double, float]
+    std::vector<void*> reexp[2];                 // per level, [double, float]
+  };
+  mutable std::mutex cache_mu;
+  mutable DevCache cache;
+  ~Plan();
 };
 
 // Per-level dense block layout for given node sizes.  Every node owns a full
@@ -123,10 +142,17 @@ struct DiagTask {        // in-place Cholesky of an n x n tile (n <= kTile) and 
 };
 
 template <typename T>
+struct FrontTask {       // blocked Cholesky of D (m x m, ld m) and L^{-1} into Li (zero on entry)
+  T* D;
+  T* Li;
+  int m, node;
+};
+
+template <typename T>
 struct QrTask {          // column-pivoted Householder QR of A (m x c, ld = m)
   T* A;                  // in/out workspace
   T* Q1;                 // out: m x r, ld = m (r = kept rank)
-  int m, c, node, pad;
+  int m, c, node, slot;  // slot: index of the rank output
 };
 
 template <typename T>
