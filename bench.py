@@ -331,6 +331,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * b_h.size},
         "clocks": clk,
     }
+    if not args.no_serve:
+        line["serve"] = run_serve(args)
     if ws == 1 and not args.no_cpu_baseline:
         cpu_ms, det = oracle_sample()
         line["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
@@ -338,6 +340,35 @@ def run_ours(args):
                                           f"({det['seconds']:.1f} s, {det['iterations']} it), scaled by n x{det['scale']:.2f}"}
     print(json.dumps(line), flush=True)
     barrier(dist)
+
+
+def run_serve(args, slots: int = 4, count: int = 256, load: float = 0.7):
+    """Serving workload: seeded Poisson stream of 3D 7-point diffusion requests
+    (edge U{32..96}, log-normal coefficients std 1, 40% factor+solve, 60%
+    solve on a resident factor, 1-8 right-hand sides) replayed in real time at
+    `load` x the measured single-slot capacity; p50/p99 latency, solves/s."""
+    from paper_1907_03406_gb300.serve import Server
+    calib = si.request_stream(seed=101, count=10, rate_hz=1e6)
+    srv = Server(slots=1)
+    srv.run(calib[:2])           # warm-up: plans, graphs, allocator
+    srv.records.clear()
+    t0 = time.perf_counter()
+    srv.run(calib[2:])
+    mean_service = (time.perf_counter() - t0) / len(calib[2:])
+    srv.close()
+    rate = load / mean_service
+    reqs = si.request_stream(seed=1, count=count, rate_hz=rate)
+    srv = Server(slots=slots)
+    summ = srv.run(reqs)
+    srv.close()
+    summ.update(load=load, rate_hz=round(rate, 3), slots=slots,
+                single_slot_service_ms=round(1e3 * mean_service, 2),
+                workload="256 requests, Poisson arrivals, edge U{32..96}, 40% factor+solve / 60% solve, "
+                         "1-8 RHS, mixed precision, rtol 1e-10")
+    for k in ("p50_ms", "p99_ms", "mean_ms", "solves_per_s", "makespan_s"):
+        if summ.get(k) is not None:
+            summ[k] = round(summ[k], 3)
+    return summ
 
 
 def run_ncu(args):
@@ -395,6 +426,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--ncu", action="store_true", help="one step in an NVTX range, for ncu")
     ap.add_argument("--workload", default=WORKLOAD, help="ncu mode: grf3d_<edge> / twophase3d_<edge>")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
