@@ -162,11 +162,10 @@ static int apply_common(const sgf_factor_t* f, const double* x, double* y, int n
   if (!f || !x || !y || nrhs < 1 || x == y) return SGF_ERR_INVALID_ARG;
   return guarded([&] {
     const int64_t n = f->f->n;
-    for (int j = 0; j < nrhs; ++j) {
-      if (which == 0) f->f->apply(x + j * n, y + j * n, (cudaStream_t)stream);
-      else if (which == 1) f->f->multiply(x + j * n, y + j * n, (cudaStream_t)stream);
-      else f->f->spmv(x + j * n, y + j * n, (cudaStream_t)stream);
-    }
+    if (which == 0) f->f->apply_n(x, y, nrhs, (cudaStream_t)stream);
+    else if (which == 1) f->f->multiply_n(x, y, nrhs, (cudaStream_t)stream);
+    else
+      for (int j = 0; j < nrhs; ++j) f->f->spmv(x + j * n, y + j * n, (cudaStream_t)stream);
     if (!sgf::dry_run()) SGF_CK(cudaGetLastError());
     return (int)SGF_OK;
   });
@@ -194,13 +193,16 @@ int sgf_pcg_solve(const sgf_factor_t* f, const double* b, double* x, int nrhs, d
     int worst = SGF_OK, itmax = 0;
     double resmax = 0;
     const int64_t n = f->f->n;
-    for (int j = 0; j < nrhs; ++j) {
-      int it = 0;
-      double rr = 0;
-      int rc = sgf::pcg_solve(*f->f, b + j * n, x + j * n, rtol, maxit, s, &it, &rr);
+    for (int j = 0; j < nrhs; j += 8) {
+      const int k = std::min(8, nrhs - j);
+      int it[8];
+      double rr[8];
+      int rc = sgf::pcg_solve_block(*f->f, b + j * n, x + j * n, k, rtol, maxit, s, it, rr);
       if (rc != SGF_OK) worst = rc;
-      itmax = std::max(itmax, it);
-      resmax = std::max(resmax, rr);
+      for (int q = 0; q < k; ++q) {
+        itmax = std::max(itmax, it[q]);
+        resmax = std::max(resmax, rr[q]);
+      }
     }
     SGF_CK(cudaEventRecord(e1, s));
     SGF_CK(cudaEventSynchronize(e1));

@@ -42,6 +42,7 @@
 #include <cstring>
 #include <initializer_list>
 #include <map>
+#include <mutex>
 #include <numeric>
 
 #include "devmem.h"
@@ -355,6 +356,8 @@ struct GemvList {
   std::vector<GemvTask<T>> t;
   std::vector<GemvContrib<T>> c;
   bool trans = false;
+  int nr = 1;  // interleaved right-hand sides
+  explicit GemvList(int nr_ = 1) : nr(nr_) {}
   struct In {
     const T* A;
     int lda;
@@ -370,7 +373,7 @@ struct GemvList {
     const int chunk = trans ? 32 : 64;
     for (int i0 = 0; i0 < M; i0 += chunk) {
       GemvTask<T> g;
-      g.y = y + i0;
+      g.y = y + (size_t)i0 * nr;
       g.M = std::min(chunk, M - i0);
       g.c_begin = (int)c.size();
       g.beta = beta;
@@ -412,11 +415,12 @@ struct GemvList {
     const size_t ot = P.b.push(t), oc = P.b.push(c);
     const int n = (int)t.size();
     const bool tr = trans;
-    P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl, by});
+    const int r = nr;
+    P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl * r, by});
     P.ops.push_back([=](const char* d, cudaStream_t s) {
-      prof_work(fl, by);
-      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, s);
-      else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, s);
+      prof_work(fl * r, by);
+      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, s);
+      else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, s);
     });
     t.clear();
     c.clear();
@@ -454,8 +458,20 @@ class FactorImpl final : public FactorBase {
   ~FactorImpl() override { release(); }
   bool mixed() const override { return sizeof(T) == 4; }
 
-  void apply(const double* x, double* y, cudaStream_t s) override { run_program(inv_, x, y, s); }
-  void multiply(const double* x, double* y, cudaStream_t s) override { run_program(fwd_, x, y, s); }
+  void apply(const double* x, double* y, cudaStream_t s) override { apply_n(x, y, 1, s); }
+  void multiply(const double* x, double* y, cudaStream_t s) override { multiply_n(x, y, 1, s); }
+  void apply_n(const double* x, double* y, int nrhs, cudaStream_t s) override { run_n(true, x, y, nrhs, s); }
+  void multiply_n(const double* x, double* y, int nrhs, cudaStream_t s) override { run_n(false, x, y, nrhs, s); }
+
+  // up to kMaxNr right-hand sides per program run (RHS-major, stride n)
+  void run_n(bool inverse, const double* x, double* y, int nrhs, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(prog_mu_);   // one program run at a time per factor
+    for (int j = 0; j < nrhs; j += kMaxNr) {
+      const int k = std::min(kMaxNr, nrhs - j);
+      const int nr = k == 1 ? 1 : k == 2 ? 2 : k <= 4 ? 4 : 8;
+      run_program(program(inverse, nr, s), nr, x + (int64_t)j * n, y + (int64_t)j * n, k, s);
+    }
+  }
   void spmv(const double* x, double* y, cudaStream_t s) override {
     launch_spmv_stencil(sd_, sx_, sy_, sz_, plan->nx, plan->ny, plan->nz, x, y, s);
   }
@@ -470,7 +486,8 @@ class FactorImpl final : public FactorBase {
   T *Ltop_ = nullptr, *Litop_ = nullptr;
   std::vector<T*> vb_;  // per non-top level: [v | w | kept], 3 * vec_size
   T* vtop_ = nullptr;   // [v | w], 2 * mtop
-  Program<T> inv_, fwd_;
+  Program<T> inv_[4], fwd_[4];   // nr = 1, 2, 4, 8 right-hand sides, built on first use
+  std::mutex prog_mu_;
 
   void release() {
     if (!dry_run()) cudaDeviceSynchronize();
@@ -478,17 +495,17 @@ class FactorImpl final : public FactorBase {
     keep_.clear();
     if (st_) dev_free(st_);
     st_ = nullptr;
-    if (!dry_run()) {
-      if (inv_.b.dev) dev_free(inv_.b.dev);
-      if (fwd_.b.dev) dev_free(fwd_.b.dev);
-      for (Program<T>* P : {&inv_, &fwd_}) {
-        if (P->exec) cudaGraphExecDestroy(P->exec);
-        if (P->graph) cudaGraphDestroy(P->graph);
+    for (int k = 0; k < 4; ++k)
+      for (Program<T>* P : {&inv_[k], &fwd_[k]}) {
+        if (!dry_run()) {
+          if (P->b.dev) dev_free(P->b.dev);
+          if (P->exec) cudaGraphExecDestroy(P->exec);
+          if (P->graph) cudaGraphDestroy(P->graph);
+        }
+        P->b.dev = nullptr;
         P->exec = nullptr;
         P->graph = nullptr;
       }
-    }
-    inv_.b.dev = fwd_.b.dev = nullptr;
   }
 
   void check_status(cudaStream_t s) {
@@ -503,9 +520,9 @@ class FactorImpl final : public FactorBase {
     }
   }
 
-  void run_program(Program<T>& P, const double* x, double* y, cudaStream_t s) {
+  void run_program(Program<T>& P, int nr, const double* x, double* y, int nrhs, cudaStream_t s) {
     T* v1 = lev_.empty() ? vtop_ : vb_[0];
-    launch_gather<T>(x, perm1_, v1, n, s);
+    launch_gather<T>(x, perm1_, v1, n, nrhs, nr, s);
     if (dry_run()) {
       for (auto& op : P.ops) op(P.b.dev, s);
     } else {
@@ -513,7 +530,7 @@ class FactorImpl final : public FactorBase {
       SGF_CK(cudaGraphLaunch(P.exec, s));
       for (const auto& a : P.acct) prof_count(a.kind, a.flops, a.bytes);
     }
-    launch_scatter<T>(v1, perm1_, y, n, s);
+    launch_scatter<T>(v1, perm1_, y, n, nrhs, nr, s);
   }
 
   // record the program's launches once on a private stream
@@ -1021,15 +1038,26 @@ class FactorImpl final : public FactorBase {
   // ----------------------------------------------------------------------
   // apply programs
   // ----------------------------------------------------------------------
+  static constexpr int kMaxNr = 8;
   void build_programs(cudaStream_t s) {
     const int nl = (int)lev_.size();
     vb_.resize(nl);
-    for (int t = 0; t < nl; ++t) vb_[t] = dalloc<T>(keep_, 3 * (size_t)std::max<int64_t>(lev_[t].lay.vec_size, 1), s);
-    vtop_ = dalloc<T>(keep_, 2 * (size_t)std::max(mtop_, 1), s);
-    build_inverse();
-    build_forward();
-    inv_.b.upload_persistent(s);
-    fwd_.b.upload_persistent(s);
+    for (int t = 0; t < nl; ++t)
+      vb_[t] = dalloc<T>(keep_, 3 * (size_t)kMaxNr * std::max<int64_t>(lev_[t].lay.vec_size, 1), s);
+    vtop_ = dalloc<T>(keep_, 2 * (size_t)kMaxNr * std::max(mtop_, 1), s);
+    program(true, 1, s);
+    program(false, 1, s);
+  }
+
+  Program<T>& program(bool inverse, int nr, cudaStream_t s) {
+    const int k = nr == 1 ? 0 : nr == 2 ? 1 : nr == 4 ? 2 : 3;
+    Program<T>& P = inverse ? inv_[k] : fwd_[k];
+    if (P.ops.empty()) {
+      if (inverse) build_inverse(P, nr);
+      else build_forward(P, nr);
+      P.b.upload_persistent(s);
+    }
+    return P;
   }
 
   T* base(int t) { return t < (int)lev_.size() ? vb_[t] : vtop_; }
@@ -1053,34 +1081,33 @@ class FactorImpl final : public FactorBase {
     });
   }
 
-  void build_inverse() {
-    Program<T>& P = inv_;
+  void build_inverse(Program<T>& P, int nr) {
     const int nl = (int)lev_.size();
     for (int t = 0; t < nl; ++t) {
       const LevelRec<T>& R = lev_[t];
       const auto& lay = R.lay;
       const int64_t vs = lay.vec_size;
       T* v = base(t);
-      T* w = v + vs;
-      T* kp = v + 2 * vs;
-      GemvList<T> f1, f2, f3, f4;
+      T* w = v + vs * nr;
+      T* kp = v + 2 * vs * nr;
+      GemvList<T> f1(nr), f2(nr), f3(nr), f4(nr);
       f2.trans = f4.trans = true;
       for (const auto& r : R.in)
-        f1.add(w + lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, v + lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+        f1.add(w + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
       auto si = sep_interiors(R, (int)lay.m.size());
       for (int S = 0; S < (int)si.size(); ++S) {
         if (si[S].empty()) continue;
         std::vector<typename GemvList<T>::In> ins;
         for (auto [a, col] : si[S]) {
           const auto& r = R.in[a];
-          ins.push_back({r.W + (size_t)col * r.m, r.m, w + lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
+          ins.push_back({r.W + (size_t)col * r.m, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
         }
-        f2.add(v + lay.vec_off[S], lay.m[S], 1, ins);
+        f2.add(v + nr * lay.vec_off[S], lay.m[S], 1, ins);
       }
       for (const auto& c : R.sep) {
         if (!c.comp) continue;
-        f3.add(w + lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, v + lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
-        f4.add(kp + lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
+        f3.add(w + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+        f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
       }
       f1.emit(P);
       f2.emit(P);
@@ -1088,14 +1115,14 @@ class FactorImpl final : public FactorBase {
       f4.emit(P);
       std::vector<VecCopyTask> vc;
       for (const auto& c : R.sep)
-        if (c.k > 0) vc.push_back({(c.comp ? 2 * vs : 0) + lay.vec_off[c.node], c.dst, c.k, 0});
+        if (c.k > 0) vc.push_back({nr * ((c.comp ? 2 * vs : 0) + lay.vec_off[c.node]), nr * c.dst, nr * c.k, 0});
       veccopy(P, vc, v, base(t + 1));
     }
     // top
     {
       T* v = vtop_;
-      T* w = vtop_ + mtop_;
-      GemvList<T> a, bt;
+      T* w = vtop_ + (size_t)mtop_ * nr;
+      GemvList<T> a(nr), bt(nr);
       bt.trans = true;
       a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1)}});
       bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
@@ -1107,26 +1134,26 @@ class FactorImpl final : public FactorBase {
       const auto& lay = R.lay;
       const int64_t vs = lay.vec_size;
       T* v = base(t);
-      T* w = v + vs;
-      T* kp = v + 2 * vs;
+      T* w = v + vs * nr;
+      T* kp = v + 2 * vs * nr;
       T* vn = base(t + 1);
       std::vector<VecCopyTask> vc;
       for (const auto& c : R.sep)
-        if (!c.comp && c.k > 0) vc.push_back({c.dst, lay.vec_off[c.node], c.k, 0});
+        if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
       veccopy(P, vc, vn, v);
-      GemvList<T> b1, b2, b3, b4;
+      GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
       b2.trans = b4.trans = true;
       for (const auto& c : R.sep) {
         if (!c.comp) continue;
-        b1.add(w + lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + c.dst, kp + lay.vec_off[c.node], c.k, false, T(1)}});
-        b2.add(v + lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+        b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
+        b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
       }
       for (const auto& r : R.in) {
         std::vector<typename GemvList<T>::In> ins;
         for (auto [S, col] : r.nb)
-          ins.push_back({r.W + (size_t)col * r.m, r.m, v + lay.vec_off[S], nullptr, lay.m[S], false, T(-1)});
-        b3.add(w + lay.vec_off[r.node], r.m, 1, ins);
-        b4.add(v + lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+          ins.push_back({r.W + (size_t)col * r.m, r.m, v + nr * lay.vec_off[S], nullptr, lay.m[S], false, T(-1)});
+        b3.add(w + nr * lay.vec_off[r.node], r.m, 1, ins);
+        b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
       }
       b1.emit(P);
       b2.emit(P);
@@ -1137,29 +1164,28 @@ class FactorImpl final : public FactorBase {
 
   // y = A_l x: the factors applied in the opposite order (G^T, B^T up, top
   // L L^T, then B, G down)
-  void build_forward() {
-    Program<T>& P = fwd_;
+  void build_forward(Program<T>& P, int nr) {
     const int nl = (int)lev_.size();
     for (int t = 0; t < nl; ++t) {
       const LevelRec<T>& R = lev_[t];
       const auto& lay = R.lay;
       const int64_t vs = lay.vec_size;
       T* v = base(t);
-      T* w = v + vs;
-      T* kp = v + 2 * vs;
-      GemvList<T> a1, a2, c1, c2;
+      T* w = v + vs * nr;
+      T* kp = v + 2 * vs * nr;
+      GemvList<T> a1(nr), a2(nr), c1(nr), c2(nr);
       a1.trans = c1.trans = c2.trans = true;
       for (const auto& r : R.in) {
-        a1.add(w + lay.vec_off[r.node], r.m, 0, {{r.L, r.m, v + lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+        a1.add(w + nr * lay.vec_off[r.node], r.m, 0, {{r.L, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
         std::vector<typename GemvList<T>::In> ins;
         for (auto [S, col] : r.nb)
-          ins.push_back({r.W + (size_t)col * r.m, r.m, v + lay.vec_off[S], nullptr, lay.m[S], false, T(1)});
-        a2.add(w + lay.vec_off[r.node], r.m, 1, ins);
+          ins.push_back({r.W + (size_t)col * r.m, r.m, v + nr * lay.vec_off[S], nullptr, lay.m[S], false, T(1)});
+        a2.add(w + nr * lay.vec_off[r.node], r.m, 1, ins);
       }
       for (const auto& c : R.sep) {
         if (!c.comp) continue;
-        c1.add(w + lay.vec_off[c.node], c.m, 0, {{c.L, c.m, v + lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
-        c2.add(kp + lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
+        c1.add(w + nr * lay.vec_off[c.node], c.m, 0, {{c.L, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+        c2.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
       }
       a1.emit(P);
       a2.emit(P);
@@ -1167,13 +1193,13 @@ class FactorImpl final : public FactorBase {
       c2.emit(P);
       std::vector<VecCopyTask> vc;
       for (const auto& c : R.sep)
-        if (c.k > 0) vc.push_back({(c.comp ? 2 * vs : 0) + lay.vec_off[c.node], c.dst, c.k, 0});
+        if (c.k > 0) vc.push_back({nr * ((c.comp ? 2 * vs : 0) + lay.vec_off[c.node]), nr * c.dst, nr * c.k, 0});
       veccopy(P, vc, v, base(t + 1));
     }
     {
       T* v = vtop_;
-      T* w = vtop_ + mtop_;
-      GemvList<T> a, bn;
+      T* w = vtop_ + (size_t)mtop_ * nr;
+      GemvList<T> a(nr), bn(nr);
       a.trans = true;
       a.add(w, mtop_, 0, {{Ltop_, mtop_, v, nullptr, mtop_, true, T(1)}});
       bn.add(v, mtop_, 0, {{Ltop_, mtop_, w, nullptr, mtop_, true, T(1)}});
@@ -1185,19 +1211,19 @@ class FactorImpl final : public FactorBase {
       const auto& lay = R.lay;
       const int64_t vs = lay.vec_size;
       T* v = base(t);
-      T* w = v + vs;
-      T* kp = v + 2 * vs;
+      T* w = v + vs * nr;
+      T* kp = v + 2 * vs * nr;
       T* vn = base(t + 1);
       std::vector<VecCopyTask> vc;
       for (const auto& c : R.sep)
-        if (!c.comp && c.k > 0) vc.push_back({c.dst, lay.vec_off[c.node], c.k, 0});
+        if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
       veccopy(P, vc, vn, v);
-      GemvList<T> b1, b2, b3, b4;
+      GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
       b3.trans = true;
       for (const auto& c : R.sep) {
         if (!c.comp) continue;
-        b1.add(w + lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + c.dst, kp + lay.vec_off[c.node], c.k, false, T(1)}});
-        b2.add(v + lay.vec_off[c.node], c.m, 0, {{c.L, c.m, w + lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+        b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
+        b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.L, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
       }
       // separators receive W^T x_I from their interiors, then x_I <- L_I x_I
       auto si = sep_interiors(R, (int)lay.m.size());
@@ -1206,12 +1232,12 @@ class FactorImpl final : public FactorBase {
         std::vector<typename GemvList<T>::In> ins;
         for (auto [a, col] : si[S]) {
           const auto& r = R.in[a];
-          ins.push_back({r.W + (size_t)col * r.m, r.m, w + lay.vec_off[r.node], nullptr, r.m, false, T(1)});
+          ins.push_back({r.W + (size_t)col * r.m, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, false, T(1)});
         }
-        b3.add(v + lay.vec_off[S], lay.m[S], 1, ins);
+        b3.add(v + nr * lay.vec_off[S], lay.m[S], 1, ins);
       }
       for (const auto& r : R.in)
-        b4.add(v + lay.vec_off[r.node], r.m, 0, {{r.L, r.m, w + lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+        b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.L, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
       b1.emit(P);
       b2.emit(P);
       b3.emit(P);
@@ -1286,6 +1312,87 @@ int pcg_solve(FactorBase& F, const double* b, double* x, double rtol, int maxit,
   *iters = it;
   *relres = tr / bnorm;
   SGF_CK(cudaFreeAsync(buf, s));
+  return rc;
+}
+
+int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double rtol, int maxit,
+                    cudaStream_t s, int* iters, double* relres) {
+  const int64_t n = F.n;
+  const int k = nrhs;
+  if (k < 1 || k > 8) throw SgfError(SGF_ERR_INVALID_ARG, "block PCG takes 1..8 right-hand sides");
+  const size_t kn = (size_t)k * n;
+  double* buf = (double*)dev_malloc_async(sizeof(double) * (5 * kn + 8 * kDotBlocks + 32), s);
+  double *r = buf, *z = r + kn, *p = z + kn, *q = p + kn, *ro = q + kn;
+  double* part = ro + kn;
+  double* sc = part + 8 * kDotBlocks;
+  double h[32];
+  // one batch of nd dot products (each over k RHS), read back with one sync
+  auto dots = [&](std::initializer_list<std::pair<const double*, const double*>> ab) {
+    int j = 0;
+    for (const auto& pr : ab) launch_dot_n(pr.first, pr.second, n, k, part, sc + 8 * j++, s);
+    dev_d2h(h, sc, sizeof(double) * 8 * j, s);
+  };
+  const bool flex = F.mixed();
+  std::vector<double> bnorm(k), rz(k);
+  std::vector<char> active(k);
+  dev_memset(x, 0, kn * sizeof(double), s);
+  dev_d2d(r, b, kn * sizeof(double), s);
+  dots({{b, b}});
+  for (int j = 0; j < k; ++j) {
+    bnorm[j] = std::sqrt(h[j]);
+    active[j] = bnorm[j] > 0.0;
+    iters[j] = 0;
+  }
+  int rc = SGF_OK;
+  F.apply_n(r, z, k, s);
+  dev_d2d(p, z, kn * sizeof(double), s);
+  dots({{r, z}});
+  for (int j = 0; j < k; ++j) rz[j] = h[j];
+  int it = 0;
+  auto any = [&] {
+    for (int j = 0; j < k; ++j)
+      if (active[j]) return true;
+    return false;
+  };
+  while (any()) {
+    if (it >= maxit) { rc = SGF_ERR_NO_CONVERGENCE; break; }
+    for (int j = 0; j < k; ++j) F.spmv(p + (size_t)j * n, q + (size_t)j * n, s);
+    dots({{p, q}});
+    Coef8 al{}, nal{};
+    for (int j = 0; j < k; ++j) {
+      const double a = active[j] ? rz[j] / h[j] : 0.0;
+      if (active[j] && !std::isfinite(a)) { rc = SGF_ERR_NONFINITE; active[j] = 0; continue; }
+      al.v[j] = active[j] ? a : 0.0;
+      nal.v[j] = -al.v[j];
+    }
+    launch_axpy_n(al, p, x, n, k, 0, s);
+    if (flex) dev_d2d(ro, r, kn * sizeof(double), s);
+    launch_axpy_n(nal, q, r, n, k, 0, s);
+    ++it;
+    for (int j = 0; j < k; ++j)
+      if (active[j]) iters[j] = it;
+    F.apply_n(r, z, k, s);
+    if (flex) dots({{r, r}, {r, z}, {z, ro}});
+    else dots({{r, r}, {r, z}});
+    Coef8 be{};
+    for (int j = 0; j < k; ++j) {
+      if (!active[j]) continue;
+      if (std::sqrt(h[j]) <= rtol * bnorm[j]) { active[j] = 0; continue; }
+      const double rzn = h[8 + j];
+      be.v[j] = flex ? (rzn - h[16 + j]) / rz[j] : rzn / rz[j];
+      rz[j] = rzn;
+    }
+    launch_axpy_n(be, z, p, n, k, 1, s);
+  }
+  // true residuals
+  for (int j = 0; j < k; ++j) F.spmv(x + (size_t)j * n, q + (size_t)j * n, s);
+  dev_d2d(r, b, kn * sizeof(double), s);
+  Coef8 m1{};
+  for (int j = 0; j < k; ++j) m1.v[j] = -1.0;
+  launch_axpy_n(m1, q, r, n, k, 0, s);
+  dots({{r, r}});
+  for (int j = 0; j < k; ++j) relres[j] = bnorm[j] > 0 ? std::sqrt(h[j]) / bnorm[j] : 0.0;
+  dev_free_async(buf, s);
   return rc;
 }
 

@@ -69,6 +69,9 @@ class FactorBase {
   virtual ~FactorBase() = default;
   virtual void apply(const double* x, double* y, cudaStream_t s) = 0;      // A_l^{-1}
   virtual void multiply(const double* x, double* y, cudaStream_t s) = 0;   // A_l
+  // nrhs vectors at once (RHS-major, stride n): every factor entry read once per 8
+  virtual void apply_n(const double* x, double* y, int nrhs, cudaStream_t s) = 0;
+  virtual void multiply_n(const double* x, double* y, int nrhs, cudaStream_t s) = 0;
   virtual void spmv(const double* x, double* y, cudaStream_t s) = 0;       // A
   virtual bool mixed() const = 0;
   const Plan* plan = nullptr;
@@ -82,5 +85,9 @@ std::unique_ptr<FactorBase> make_factor(const Plan& plan, const double* coeffs_d
 // PCG (Sec. 7) on an existing factor; returns SGF_OK or SGF_ERR_NO_CONVERGENCE
 int pcg_solve(FactorBase& F, const double* b, double* x, double rtol, int maxit, cudaStream_t s,
               int* iters, double* relres);
+// nrhs (<= 8) independent PCG recurrences advanced together (one apply per
+// iteration for all of them); iters/relres per RHS
+int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double rtol, int maxit,
+                    cudaStream_t s, int* iters, double* relres);
 
 }  // namespace sgf

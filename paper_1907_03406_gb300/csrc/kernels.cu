@@ -575,61 +575,91 @@ __global__ void __launch_bounds__(kThreads) k_qrcp(const QrTask<T>* __restrict__
 // ---------------------------------------------------------------------------
 // batched GEMV
 // ---------------------------------------------------------------------------
-// op(A) = A: chunk of <= 64 output rows; 4 groups of 64 threads split the columns
-template <typename T>
+// op(A) = A: chunk of <= 64 output rows; 4 groups of 64 threads split the
+// columns.  NR right-hand sides are interleaved (element i of RHS q at
+// i * NR + q), so each matrix entry is read once for all of them.
+template <typename T, int NR>
 __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restrict__ tasks,
                                                      const GemvContrib<T>* __restrict__ cons) {
   const GemvTask<T> tk = tasks[blockIdx.x];
   const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
-  T acc = T(0);
+  T acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = T(0);
   if (r < tk.M) {
     for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
       const GemvContrib<T> cb = cons[c];
       int kend = cb.K;
       if (cb.tri) kend = min(kend, cb.tri - 1 + r + 1);  // lower triangular: j <= row
       const T* a = cb.A + r;
-      T part = T(0);
+      T part[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) part[q] = T(0);
 #pragma unroll 4
       for (int j = g; j < kend; j += 4) {
-        T xv = cb.x[j];
-        if (cb.x2) xv -= cb.x2[j];
-        part = fma(a[(size_t)j * cb.lda], xv, part);
+        const T av = a[(size_t)j * cb.lda];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          T xv = cb.x[(size_t)j * NR + q];
+          if (cb.x2) xv -= cb.x2[(size_t)j * NR + q];
+          part[q] = fma(av, xv, part[q]);
+        }
       }
-      acc = fma(cb.alpha, part, acc);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = fma(cb.alpha, part[q], acc[q]);
     }
   }
-  __shared__ T red[4][64];
-  red[g][r] = acc;
+  __shared__ T red[4][64][NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) red[g][r][q] = acc[q];
   __syncthreads();
   if (g == 0 && r < tk.M) {
-    const T s = (red[0][r] + red[1][r]) + (red[2][r] + red[3][r]);
-    tk.y[r] = tk.beta ? tk.y[r] + s : s;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const T v = (red[0][r][q] + red[1][r][q]) + (red[2][r][q] + red[3][r][q]);
+      T* y = tk.y + (size_t)r * NR + q;
+      *y = tk.beta ? *y + v : v;
+    }
   }
 }
 
 // op(A) = A^T: chunk of <= 32 outputs (columns of A); one warp per output
-template <typename T>
+template <typename T, int NR>
 __global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restrict__ tasks,
                                                      const GemvContrib<T>* __restrict__ cons) {
   const GemvTask<T> tk = tasks[blockIdx.x];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = warp; o < tk.M; o += kThreads / 32) {
-    T acc = T(0);
+    T acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = T(0);
     for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
       const GemvContrib<T> cb = cons[c];
       const int i0 = cb.tri ? (cb.tri - 1 + o) : 0;  // lower triangular: i >= column
       const T* a = cb.A + (size_t)o * cb.lda;
-      T part = T(0);
+      T part[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) part[q] = T(0);
 #pragma unroll 4
       for (int i = i0 + lane; i < cb.K; i += 32) {
-        T xv = cb.x[i];
-        if (cb.x2) xv -= cb.x2[i];
-        part = fma(a[i], xv, part);
+        const T av = a[i];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          T xv = cb.x[(size_t)i * NR + q];
+          if (cb.x2) xv -= cb.x2[(size_t)i * NR + q];
+          part[q] = fma(av, xv, part[q]);
+        }
       }
-      part = warp_sum(part);
-      acc = fma(cb.alpha, part, acc);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = fma(cb.alpha, warp_sum(part[q]), acc[q]);
     }
-    if (lane == 0) tk.y[o] = tk.beta ? tk.y[o] + acc : acc;
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        T* y = tk.y + (size_t)o * NR + q;
+        *y = tk.beta ? *y + acc[q] : acc[q];
+      }
+    }
   }
 }
 
@@ -730,18 +760,70 @@ __global__ void k_dot_final(const double* __restrict__ partials, int np, double*
   }
 }
 
+// natural-order RHS-major vectors <-> interleaved level-1 vectors
+// nrhs dot products a_q . b_q (RHS-major vectors of length n), the same
+// fixed-order reduction per RHS as k_dot_partial / k_dot_final
+__global__ void k_dot_partial_n(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                double* __restrict__ partials) {
+  const int q = blockIdx.y;
+  const double* aq = a + (int64_t)q * n;
+  const double* bq = b + (int64_t)q * n;
+  double s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    s = fma(aq[i], bq[i], s);
+  s = warp_sum(s);
+  __shared__ double w[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < kThreads / 32; ++k) t += w[k];
+    partials[(int64_t)q * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_dot_final_n(const double* __restrict__ partials, int np, double* result) {
+  const int q = blockIdx.x;
+  double s = 0;
+  for (int i = threadIdx.x; i < np; i += kThreads) s += partials[(int64_t)q * np + i];
+  s = warp_sum(s);
+  __shared__ double w[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < kThreads / 32; ++k) t += w[k];
+    result[q] = t;
+  }
+}
+
+// y_q = a_q x_q + y_q for q < nrhs (mode 0); p_q = z_q + a_q p_q (mode 1)
+__global__ void k_axpy_n(Coef8 a, const double* __restrict__ x, double* __restrict__ y, int64_t n, int nrhs,
+                         int mode) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < nrhs; ++q) {
+    const int64_t k = (int64_t)q * n + i;
+    y[k] = mode == 0 ? fma(a.v[q], x[k], y[k]) : fma(a.v[q], y[k], x[k]);
+  }
+}
+
 template <typename T>
 __global__ void k_gather(const double* __restrict__ src, const int64_t* __restrict__ perm,
-                         T* __restrict__ dst, int64_t n) {
+                         T* __restrict__ dst, int64_t n, int nrhs, int nr) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (T)src[perm[i]];
+  if (i >= n) return;
+  const int64_t p = perm[i];
+  for (int q = 0; q < nr; ++q) dst[i * nr + q] = q < nrhs ? (T)src[(int64_t)q * n + p] : T(0);
 }
 
 template <typename T>
 __global__ void k_scatter(const T* __restrict__ src, const int64_t* __restrict__ perm,
-                          double* __restrict__ dst, int64_t n) {
+                          double* __restrict__ dst, int64_t n, int nrhs, int nr) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[perm[i]] = (double)src[i];
+  if (i >= n) return;
+  const int64_t p = perm[i];
+  for (int q = 0; q < nrhs; ++q) dst[(int64_t)q * n + p] = (double)src[i * nr + q];
 }
 
 __global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
@@ -864,35 +946,45 @@ void launch_qrcp(const QrTask<T>* tasks, int n, int* ranks, double tau, int max_
 }
 
 template <typename T>
-static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, bool trans) {
+static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, bool trans, int nr) {
   for (int i = 0; i < n; ++i) {
     const GemvTask<T>& t = tasks[i];
     if (t.M > (trans ? 32 : 64) || t.M < 1) check_range(nullptr, 1, "gemv chunk shape");
-    check_range(t.y, sizeof(T) * t.M, "gemv y");
+    check_range(t.y, sizeof(T) * t.M * nr, "gemv y");
     for (int c = t.c_begin; c < t.c_begin + t.c_count; ++c) {
       const GemvContrib<T>& q = cons[c];
       if (trans) check_block(q.A, q.K, t.M, q.lda, sizeof(T), "gemvT A");
       else check_block(q.A, t.M, q.K, q.lda, sizeof(T), "gemv A");
-      check_range(q.x, sizeof(T) * q.K, "gemv x");
-      if (q.x2) check_range(q.x2, sizeof(T) * q.K, "gemv x2");
+      check_range(q.x, sizeof(T) * q.K * nr, "gemv x");
+      if (q.x2) check_range(q.x2, sizeof(T) * q.K * nr, "gemv x2");
     }
   }
 }
 
 template <typename T>
-void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, false);
+void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, cudaStream_t s) {
+  if (dry_run()) return check_gemv(tasks, cons, n, false, nr);
   if (n <= 0) return;
   ProfScope ps(P_GEMV_N, s);
-  k_gemv_n<T><<<n, kThreads, 0, s>>>(tasks, cons);
+  switch (nr) {
+    case 1: k_gemv_n<T, 1><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    case 2: k_gemv_n<T, 2><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    case 4: k_gemv_n<T, 4><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    default: k_gemv_n<T, 8><<<n, kThreads, 0, s>>>(tasks, cons); break;
+  }
 }
 
 template <typename T>
-void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, true);
+void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, cudaStream_t s) {
+  if (dry_run()) return check_gemv(tasks, cons, n, true, nr);
   if (n <= 0) return;
   ProfScope ps(P_GEMV_T, s);
-  k_gemv_t<T><<<n, kThreads, 0, s>>>(tasks, cons);
+  switch (nr) {
+    case 1: k_gemv_t<T, 1><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    case 2: k_gemv_t<T, 2><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    case 4: k_gemv_t<T, 4><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    default: k_gemv_t<T, 8><<<n, kThreads, 0, s>>>(tasks, cons); break;
+  }
 }
 
 template <typename T>
@@ -942,28 +1034,46 @@ void launch_dot(const double* a, const double* b, int64_t n, double* partials, d
 }
 
 template <typename T>
-void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, cudaStream_t s) {
+void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, int nrhs, int nr,
+                   cudaStream_t s) {
   if (dry_run()) {
     check_range(perm, 8 * n, "gather perm");
-    check_range(dst, sizeof(T) * n, "gather dst");
+    check_range(dst, sizeof(T) * n * nr, "gather dst");
     return;
   }
   if (n <= 0) return;
-  prof_work(0, (16.0 + sizeof(T)) * n);
+  prof_work(0, (8.0 + (8.0 + sizeof(T)) * nrhs) * n);
   ProfScope ps(P_VEC, s);
-  k_gather<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n);
+  k_gather<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n, nrhs, nr);
 }
 template <typename T>
-void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, cudaStream_t s) {
+void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, int nrhs, int nr,
+                    cudaStream_t s) {
   if (dry_run()) {
     check_range(perm, 8 * n, "scatter perm");
-    check_range(src, sizeof(T) * n, "scatter src");
+    check_range(src, sizeof(T) * n * nr, "scatter src");
     return;
   }
   if (n <= 0) return;
-  prof_work(0, (16.0 + sizeof(T)) * n);
+  prof_work(0, (8.0 + (8.0 + sizeof(T)) * nrhs) * n);
   ProfScope ps(P_VEC, s);
-  k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n);
+  k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n, nrhs, nr);
+}
+
+void launch_dot_n(const double* a, const double* b, int64_t n, int nrhs, double* partials, double* result,
+                  cudaStream_t s) {
+  if (dry_run() || nrhs <= 0) return;
+  prof_work(2.0 * n * nrhs, 16.0 * n * nrhs);
+  ProfScope ps(P_DOT, s);
+  k_dot_partial_n<<<dim3(kDotBlocks, nrhs), kThreads, 0, s>>>(a, b, n, partials);
+  k_dot_final_n<<<nrhs, kThreads, 0, s>>>(partials, kDotBlocks, result);
+}
+
+void launch_axpy_n(const Coef8& a, const double* x, double* y, int64_t n, int nrhs, int mode, cudaStream_t s) {
+  if (dry_run() || n <= 0 || nrhs <= 0) return;
+  prof_work(2.0 * n * nrhs, 24.0 * n * nrhs);
+  ProfScope ps(P_VEC, s);
+  k_axpy_n<<<blocks_for(n), kThreads, 0, s>>>(a, x, y, n, nrhs, mode);
 }
 
 void launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s) {
@@ -988,14 +1098,18 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
   template void launch_copy<T, T>(const CopyTask<T, T>*, int, cudaStream_t);                    \
   template void launch_qrcp<T>(const QrTask<T>*, int, int*, double, int, int, long long,        \
                                cudaStream_t);                                                    \
-  template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, cudaStream_t); \
-  template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, cudaStream_t); \
+  template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int,           \
+                                 cudaStream_t);                                                  \
+  template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int,           \
+                                 cudaStream_t);                                                  \
   template void launch_veccopy<T>(const VecCopyTask*, int, const T*, T*, cudaStream_t);         \
   template void launch_assemble_scalar<T>(const double*, int, int, int, unsigned, double,       \
                                           const int64_t*, int64_t, T*, T*, double*, double*,    \
                                           double*, double*, cudaStream_t);                       \
-  template void launch_gather<T>(const double*, const int64_t*, T*, int64_t, cudaStream_t);     \
-  template void launch_scatter<T>(const T*, const int64_t*, double*, int64_t, cudaStream_t);
+  template void launch_gather<T>(const double*, const int64_t*, T*, int64_t, int, int,          \
+                                 cudaStream_t);                                                  \
+  template void launch_scatter<T>(const T*, const int64_t*, double*, int64_t, int, int,         \
+                                  cudaStream_t);
 
 SGF_INST(double)
 SGF_INST(float)

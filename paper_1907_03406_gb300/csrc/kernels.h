@@ -31,11 +31,12 @@ template <typename T>
 void launch_qrcp(const QrTask<T>* tasks, int ntasks, int* ranks, double tau, int max_m, int max_c,
                  long long cap_elems, cudaStream_t s);
 size_t qr_smem_bytes(int m, int c, size_t elem_size, long long cap_elems);
+// nr right-hand sides interleaved (nr in 1, 2, 4, 8)
 template <typename T>
-void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks,
+void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr,
                    cudaStream_t s);
 template <typename T>
-void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks,
+void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr,
                    cudaStream_t s);
 template <typename T>
 void launch_veccopy(const VecCopyTask* tasks, int ntasks, const T* src, T* dst, cudaStream_t s);
@@ -57,10 +58,23 @@ constexpr int kDotBlocks = 304;
 void launch_dot(const double* a, const double* b, int64_t n, double* partials, double* result,
                 cudaStream_t s);
 
+// natural-order RHS-major (nrhs x n) <-> interleaved level-1 vectors (nr >= nrhs)
 template <typename T>
-void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, cudaStream_t s);
+void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, int nrhs, int nr,
+                   cudaStream_t s);
 template <typename T>
-void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, cudaStream_t s);
+void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, int nrhs, int nr,
+                    cudaStream_t s);
+
+// block PCG helpers on RHS-major FP64 vectors (nrhs <= 8)
+struct Coef8 {
+  double v[8];
+};
+void launch_dot_n(const double* a, const double* b, int64_t n, int nrhs, double* partials,
+                  double* result, cudaStream_t s);  // partials: nrhs * kDotBlocks
+// mode 0: y_q += a_q x_q ; mode 1: y_q = x_q + a_q y_q
+void launch_axpy_n(const Coef8& a, const double* x, double* y, int64_t n, int nrhs, int mode,
+                   cudaStream_t s);
 
 // y = a*x + y (FP64)
 void launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s);

@@ -30,6 +30,9 @@ for (n, dim, st, dm, leaf, deg, prec, scheme) in json.loads(sys.argv[1]):
     rc = lib.sgf_factor(P.handle, C.c_void_p(4096), None, C.byref(h))
     rc2 = lib.sgf_apply(h, C.c_void_p(8192), C.c_void_p(16384), 1, None) if rc == 0 else -99
     rc3 = lib.sgf_apply_forward(h, C.c_void_p(8192), C.c_void_p(16384), 1, None) if rc == 0 else -99
+    for nrhs in (2, 3, 8, 11):     # interleaved multi-RHS programs
+        if rc == 0:
+            rc2 = rc2 or lib.sgf_apply(h, C.c_void_p(8192), C.c_void_p(16384), nrhs, None)
     v = lib.sgf_dry_run_violations(0)
     rep = lib.sgf_dry_run_report().decode()
     if rc == 0:

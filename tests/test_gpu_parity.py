@@ -219,3 +219,25 @@ def test_full_size_64cube_apply_and_iterations():
     _, it_o, _ = pcg(lambda q: A @ q, O.solve, b)
     assert abs(info["iterations"] - it_o) <= 1
     assert info["rel_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multi_rhs_apply_and_block_pcg_equal_single_rhs(precision):
+    # several right-hand sides share one pass over the factor; each must get
+    # exactly the single-RHS answer (same arithmetic per RHS)
+    cfg = _problem("grf3d_24")
+    plan, F = _gpu(cfg, precision=precision)
+    rng = np.random.default_rng(9)
+    for k in (3, 8, 11):
+        X = rng.standard_normal((k, plan.n))
+        Y = F.apply(_t(X.ravel())).cpu().numpy().reshape(k, plan.n)
+        for j in range(k):
+            y1 = F.apply(_t(X[j])).cpu().numpy()
+            assert np.array_equal(Y[j], y1)
+    B = si.rhs(plan.n, 4, nrhs=5)
+    x, info = F.pcg(_t(B.ravel()), rtol=1e-10, maxit=500)
+    x = x.cpu().numpy().reshape(5, plan.n)
+    assert info["rel_residual"] <= 1e-10
+    for j in range(5):
+        x1, info1 = F.pcg(_t(B[j]), rtol=1e-10, maxit=500)
+        assert np.array_equal(x[j], x1.cpu().numpy())
