@@ -22,7 +22,11 @@
  *    number x + nx*(y + ny*z), and DOF c of a vector problem is 3*point + c.
  *    Several right-hand sides are stored one after the other (nrhs x n,
  *    row-major: RHS j starts at j*n).
- *  - Coefficient arrays are FP64 per cell in the same natural order.
+ *  - Coefficient arrays are FP64 per cell in the same natural order; for Q1
+ *    elasticity one Young's modulus per hexahedral element (ex x ey x ez,
+ *    x fastest) where the point grid is ex x (ey+1) x (ez+1) free nodes (the
+ *    nodes of the clamped x = 0 face are removed; point x index i is node
+ *    x = i + 1).
  */
 #ifndef SGF_H_
 #define SGF_H_
@@ -52,7 +56,7 @@ typedef enum {
   SGF_STENCIL_5PT_2D = 0,    /* FD Laplacian -div(k grad u), ghost Dirichlet (weight 1)   */
   SGF_STENCIL_7PT_3D = 1,    /* FD 7-point, ghost Dirichlet (weight 1)                    */
   SGF_STENCIL_7PT_FV_3D = 2, /* two-point-flux finite volume, half-cell Dirichlet (w 2)   */
-  SGF_STENCIL_Q1_ELASTIC_3D = 3 /* trilinear hexahedra, 3 DOF / node (not in this build) */
+  SGF_STENCIL_Q1_ELASTIC_3D = 3 /* trilinear hexahedra, 3 DOF / node, x- face clamped    */
 } sgf_stencil;
 
 /* Dirichlet face bits; every other face is natural (Neumann / no flow). */
@@ -84,6 +88,7 @@ typedef struct sgf_opts {
   int precision;           /* sgf_precision                                     */
   double tau;              /* rank tolerance: keep |R_kk| > tau |R_11|; <=0 = default */
   int compress_from_level; /* first level whose separators may compress (>= 1)  */
+  double nu;               /* Poisson ratio for Q1 elasticity (<= 0: 0.3)       */
 } sgf_opts;
 
 typedef struct sgf_plan sgf_plan;
@@ -95,7 +100,10 @@ typedef struct sgf_factor_s sgf_factor_t;
  * node orders, parent/child maps and block sparsity of every level, the
  * node-local polynomial bases Pi^j of Sec. 3.1 and the re-expansion matrices
  * used when nodes merge (Sec. 4.4).  Host only; no device work.
- * Errors: INVALID_ARG for bad sizes/options, UNSUPPORTED for elasticity.  */
+ * Q1 elasticity (Sec. 7.1.3 on hexahedra): dof = 3, the rigid-body-mode
+ * basis (Sec. 7.2), the x- face clamped.
+ * Errors: INVALID_ARG for bad sizes/options, UNSUPPORTED for combinations
+ * this build does not implement.                                            */
 int sgf_analyze(const sgf_grid* grid, int stencil, const sgf_opts* opts, sgf_plan** out);
 void sgf_plan_destroy(sgf_plan* plan);
 

@@ -177,4 +177,8 @@ def assemble(cfg: dict):
         return assemble_scalar(cfg["n"], 3, cfg["coeffs"], cfg["dirichlet"], 2.0)
     if st == "7pt_3d":
         return assemble_scalar(cfg["n"], 3, cfg["coeffs"], cfg["dirichlet"], 1.0)
+    if st == "q1_elastic_3d":
+        K, pts = assemble_elastic(cfg["elems"], cfg["coeffs"], cfg.get("nu", 0.3), clamp_xm=True)
+        assert tuple(pts) == tuple(cfg["n"])
+        return K
     raise KeyError(st)

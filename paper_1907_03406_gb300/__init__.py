@@ -55,7 +55,7 @@ class Plan:
 
     def __init__(self, n, dim: int, stencil: str, dirichlet: int, leaf: int, degree: int,
                  scheme: str = "nest_all_all", precision: str = "fp64", tau: float = 0.0,
-                 compress_from_level: int = 1, basis: int = 0, dof: int = 1):
+                 compress_from_level: int = 1, basis: int = 0, dof: int = 1, nu: float = 0.0):
         self._lib = L.load()
         g = L.sgf_grid()
         g.dim = dim
@@ -71,6 +71,7 @@ class Plan:
         o.precision = PRECISIONS[precision]
         o.tau = float(tau)
         o.compress_from_level = int(compress_from_level)
+        o.nu = float(nu)
         h = C.c_void_p()
         _check(self._lib.sgf_analyze(C.byref(g), STENCILS[stencil], C.byref(o), C.byref(h)), "sgf_analyze")
         self.handle = h
@@ -82,6 +83,10 @@ class Plan:
 
     @classmethod
     def from_config(cls, cfg: dict, **kw):
+        kw.setdefault("basis", 1 if cfg.get("basis") == "rbm" else 0)
+        kw.setdefault("dof", cfg.get("dof", 1))
+        if "nu" in cfg:
+            kw.setdefault("nu", cfg["nu"])
         return cls(cfg["n"], cfg["dim"], cfg["stencil"], cfg["dirichlet"], cfg["leaf"],
                    cfg["degree"], **kw)
 

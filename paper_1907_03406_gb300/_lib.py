@@ -18,7 +18,8 @@ class sgf_grid(C.Structure):
 
 class sgf_opts(C.Structure):
     _fields_ = [("scheme", C.c_int), ("leaf", C.c_int), ("degree", C.c_int), ("basis", C.c_int),
-                ("precision", C.c_int), ("tau", C.c_double), ("compress_from_level", C.c_int)]
+                ("precision", C.c_int), ("tau", C.c_double), ("compress_from_level", C.c_int),
+                ("nu", C.c_double)]
 
 
 class sgf_solve_info(C.Structure):

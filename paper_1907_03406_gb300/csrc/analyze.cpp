@@ -26,6 +26,7 @@
 #include <map>
 #include <numeric>
 #include <unordered_set>
+#include <vector>
 
 #include "sgf_internal.h"
 
@@ -137,6 +138,77 @@ void reexpansion(const int* cbox, const int* pbox, const std::vector<std::array<
   }
 }
 
+// one isotropic scale per node keeps rotations rigid (1 for a single point)
+void frame_rbm(const int* box, double c[3], double& s) {
+  double h[3];
+  frame_of(box, c, h);
+  s = std::max(h[0], std::max(h[1], h[2]));
+  if (!(s > 0)) s = 1.0;
+}
+
+// R (6 x 6, col-major): parent modes in the child's; u_parent = a u_child + b
+void reexpansion_rbm(const int* cbox, const int* pbox, double* R) {
+  double cc[3], cp[3], sc, sp;
+  frame_rbm(cbox, cc, sc);
+  frame_rbm(pbox, cp, sp);
+  const double a = sc / sp;
+  double b[3];
+  for (int k = 0; k < 3; ++k) b[k] = (cc[k] - cp[k]) / sp;
+  std::fill(R, R + 36, 0.0);
+  for (int k = 0; k < 3; ++k) R[k + 6 * k] = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    R[(3 + k) + 6 * (3 + k)] = a;
+    // e_k x b in the translation rows of column 3 + k
+    const int i = (k + 1) % 3, j = (k + 2) % 3;
+    R[i + 6 * (3 + k)] = -b[j];
+    R[j + 6 * (3 + k)] = b[i];
+  }
+}
+
+// 24 x 24 stiffness (row-major) of a unit-cube trilinear hexahedron with
+// E = 1: B^T D B integrated by the 2 x 2 x 2 Gauss rule; node a at corner
+// (a & 1, (a >> 1) & 1, (a >> 2) & 1), DOF 3 a + component.
+void q1_element_stiffness(double nu, std::vector<double>& K) {
+  const double lam = nu / ((1 + nu) * (1 - 2 * nu)), mu = 1.0 / (2 * (1 + nu));
+  double D[6][6] = {};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) D[i][j] = lam + (i == j ? 2 * mu : 0.0);
+  D[3][3] = D[4][4] = D[5][5] = mu;
+  const double g[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+  K.assign(24 * 24, 0.0);
+  for (int gi = 0; gi < 8; ++gi) {
+    const double pt[3] = {g[gi & 1], g[(gi >> 1) & 1], g[(gi >> 2) & 1]};
+    double Bm[6][24] = {};
+    for (int a = 0; a < 8; ++a) {
+      double f[3], sg[3];
+      for (int d = 0; d < 3; ++d) {
+        const int cor = (a >> d) & 1;
+        f[d] = cor ? pt[d] : 1.0 - pt[d];
+        sg[d] = cor ? 1.0 : -1.0;
+      }
+      const double dx = sg[0] * f[1] * f[2], dy = f[0] * sg[1] * f[2], dz = f[0] * f[1] * sg[2];
+      const int c = 3 * a;
+      Bm[0][c] = dx; Bm[1][c + 1] = dy; Bm[2][c + 2] = dz;
+      Bm[3][c] = dy; Bm[3][c + 1] = dx;
+      Bm[4][c + 1] = dz; Bm[4][c + 2] = dy;
+      Bm[5][c] = dz; Bm[5][c + 2] = dx;
+    }
+    double DB[6][24];
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 24; ++j) {
+        double acc = 0;
+        for (int k = 0; k < 6; ++k) acc += D[i][k] * Bm[k][j];
+        DB[i][j] = acc;
+      }
+    for (int i = 0; i < 24; ++i)
+      for (int j = 0; j < 24; ++j) {
+        double acc = 0;
+        for (int k = 0; k < 6; ++k) acc += Bm[k][i] * DB[k][j];
+        K[i * 24 + j] += 0.125 * acc;   // Gauss weight (1/2)^3
+      }
+  }
+}
+
 }  // namespace
 
 int LevelLayout::col_of(int u, int v) const {
@@ -194,20 +266,25 @@ void build_layout(const LevelSym& L, const std::vector<int>& m, LevelLayout& o) 
 
 int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::string& err) {
   if (!g || !op) { err = "null argument"; return SGF_ERR_INVALID_ARG; }
-  if (stencil == SGF_STENCIL_Q1_ELASTIC_3D) {
-    err = "Q1 elasticity is not implemented in this build";
-    return SGF_ERR_UNSUPPORTED;
-  }
   if (stencil < 0 || stencil > SGF_STENCIL_Q1_ELASTIC_3D) { err = "bad stencil"; return SGF_ERR_INVALID_ARG; }
   const int dim = g->dim;
   if (dim != 2 && dim != 3) { err = "dim must be 2 or 3"; return SGF_ERR_INVALID_ARG; }
   if ((stencil == SGF_STENCIL_5PT_2D) != (dim == 2)) { err = "stencil/dim mismatch"; return SGF_ERR_INVALID_ARG; }
-  if (g->dof != 1) { err = "only scalar problems (dof = 1) in this build"; return SGF_ERR_UNSUPPORTED; }
+  const bool elastic = stencil == SGF_STENCIL_Q1_ELASTIC_3D;
+  if (elastic) {
+    if (g->dof != 3) { err = "Q1 elasticity has 3 DOFs per point"; return SGF_ERR_INVALID_ARG; }
+    if (op->basis != SGF_BASIS_RBM) { err = "Q1 elasticity uses the rigid-body-mode basis"; return SGF_ERR_UNSUPPORTED; }
+    if (g->dirichlet != SGF_FACE_XM) { err = "Q1 elasticity: only the clamped x- face"; return SGF_ERR_UNSUPPORTED; }
+    if (g->n[1] < 2 || g->n[2] < 2) { err = "Q1 elasticity needs >= 2 nodes in y and z"; return SGF_ERR_INVALID_ARG; }
+  } else if (g->dof != 1) {
+    err = "scalar stencils have 1 DOF per point";
+    return SGF_ERR_INVALID_ARG;
+  }
   for (int a = 0; a < dim; ++a)
     if (g->n[a] < 1 || g->n[a] > (1 << 14)) { err = "grid size out of range"; return SGF_ERR_INVALID_ARG; }
   if (op->leaf < 2) { err = "leaf must be >= 2"; return SGF_ERR_INVALID_ARG; }
   if (op->degree < 0 || op->degree > 2) { err = "degree must be 0, 1 or 2"; return SGF_ERR_INVALID_ARG; }
-  if (op->basis != SGF_BASIS_POLY) { err = "only the polynomial basis for scalar problems"; return SGF_ERR_UNSUPPORTED; }
+  if (!elastic && op->basis != SGF_BASIS_POLY) { err = "scalar problems use the polynomial basis"; return SGF_ERR_UNSUPPORTED; }
   if (op->scheme < 0 || op->scheme > 2) { err = "bad scheme"; return SGF_ERR_INVALID_ARG; }
   if (op->precision != SGF_PREC_FP64 && op->precision != SGF_PREC_MIXED) { err = "bad precision"; return SGF_ERR_INVALID_ARG; }
 
@@ -222,7 +299,9 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
   P.dof = g->dof;
   P.n = P.npts * P.dof;
   const auto ex = exponents(dim, op->degree);
-  P.pi = (int)ex.size();
+  P.pi = elastic ? 6 : (int)ex.size();
+  P.nu = op->nu > 0 ? op->nu : 0.3;
+  if (elastic && !(P.nu < 0.5)) { err = "Poisson ratio must be < 0.5"; return SGF_ERR_INVALID_ARG; }
   P.tau = op->tau > 0 ? op->tau : (op->precision == SGF_PREC_MIXED ? 1e-6 : 1e-12);
   const int N[3] = {P.nx, P.ny, P.nz};
 
@@ -415,9 +494,26 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
     const LevelSym& L1 = P.lev[0];
     P.phi1_off.assign(L1.nnodes + 1, 0);
     for (int i = 0; i < L1.nnodes; ++i)
-      P.phi1_off[i + 1] = P.phi1_off[i] + (int64_t)(L1.pt_ptr[i + 1] - L1.pt_ptr[i]) * P.pi;
+      P.phi1_off[i + 1] = P.phi1_off[i] + (int64_t)(L1.pt_ptr[i + 1] - L1.pt_ptr[i]) * P.dof * P.pi;
     P.phi1.assign(P.phi1_off.back(), 0.0);
-    for (int i = 0; i < L1.nnodes; ++i) {
+    for (int i = 0; elastic && i < L1.nnodes; ++i) {
+      // rigid-body modes (Sec. 7.2): translations, rotations about x, y, z in
+      // local coordinates (x - c) / s with one scale per node
+      double c[3], s;
+      frame_rbm(&L1.box[6 * i], c, s);
+      const int np = L1.pt_ptr[i + 1] - L1.pt_ptr[i], m = 3 * np;
+      double* F = &P.phi1[P.phi1_off[i]];
+      for (int r = 0; r < np; ++r) {
+        const int64_t p = L1.pt_idx[L1.pt_ptr[i] + r];
+        const double u = ((double)(p % P.nx) - c[0]) / s, v = ((double)((p / P.nx) % P.ny) - c[1]) / s,
+                     w = ((double)(p / ((int64_t)P.nx * P.ny)) - c[2]) / s;
+        for (int k = 0; k < 3; ++k) F[3 * r + k + (size_t)m * k] = 1.0;
+        F[3 * r + 1 + (size_t)m * 3] = -w; F[3 * r + 2 + (size_t)m * 3] = v;
+        F[3 * r + 0 + (size_t)m * 4] = w;  F[3 * r + 2 + (size_t)m * 4] = -u;
+        F[3 * r + 0 + (size_t)m * 5] = -v; F[3 * r + 1 + (size_t)m * 5] = u;
+      }
+    }
+    for (int i = 0; !elastic && i < L1.nnodes; ++i) {
       double c[3], h[3];
       frame_of(&L1.box[6 * i], c, h);
       const int m = L1.pt_ptr[i + 1] - L1.pt_ptr[i];
@@ -436,8 +532,11 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
       const LevelSym& pv = P.lev[li - 1];
       L.reexp.assign(L.child_idx.size() * (size_t)P.pi * P.pi, 0.0);
       for (int D = 0; D < L.nnodes; ++D)
-        for (int k = L.child_ptr[D]; k < L.child_ptr[D + 1]; ++k)
-          reexpansion(&pv.box[6 * L.child_idx[k]], &L.box[6 * D], ex, &L.reexp[(size_t)k * P.pi * P.pi]);
+        for (int k = L.child_ptr[D]; k < L.child_ptr[D + 1]; ++k) {
+          double* R = &L.reexp[(size_t)k * P.pi * P.pi];
+          if (elastic) reexpansion_rbm(&pv.box[6 * L.child_idx[k]], &L.box[6 * D], R);
+          else reexpansion(&pv.box[6 * L.child_idx[k]], &L.box[6 * D], ex, R);
+        }
     }
   }
 
@@ -445,6 +544,15 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
   for (auto& L : P.lev) {
     L.act.assign(L.nnodes, 0);
     for (int i = 0; i < L.nnodes; ++i) {
+      if (elastic) {
+        // translations, plus a rotation about axis k when another axis varies
+        bool var[3];
+        for (int a = 0; a < 3; ++a) var[a] = L.box[6 * i + a] != L.box[6 * i + 3 + a];
+        int cnt = 3;
+        for (int k = 0; k < 3; ++k) cnt += var[(k + 1) % 3] || var[(k + 2) % 3];
+        L.act[i] = cnt;
+        continue;
+      }
       int cnt = 0;
       for (const auto& e : ex) {
         bool ok = true;
@@ -456,8 +564,46 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
     }
   }
 
-  // ---- level-1 assembly destinations (scalar stencils) ------------------
-  {
+  // ---- level-1 assembly destinations -----------------------------------
+  if (elastic) {
+    const LevelSym& L1 = P.lev[0];
+    std::vector<int> m1(L1.nnodes);
+    for (int i = 0; i < L1.nnodes; ++i) m1[i] = (L1.pt_ptr[i + 1] - L1.pt_ptr[i]) * 3;
+    LevelLayout lay;
+    build_layout(L1, m1, lay);
+    std::vector<int> node_of(P.npts), lpos(P.npts);
+    P.perm1.assign(P.n, 0);
+    for (int u = 0; u < L1.nnodes; ++u)
+      for (int k = L1.pt_ptr[u]; k < L1.pt_ptr[u + 1]; ++k) {
+        const int p = L1.pt_idx[k];
+        node_of[p] = u;
+        lpos[p] = k - L1.pt_ptr[u];
+        for (int c = 0; c < 3; ++c) P.perm1[lay.vec_off[u] + 3 * lpos[p] + c] = 3 * (int64_t)p + c;
+      }
+    // per point and neighbour offset (dx + 3 dy + 9 dz over {-1,0,1}^3): the
+    // offset of the 3x3 block's (0, 0) entry in [diagonal blocks | panels]
+    P.asm_map.assign(P.npts * 27, -1);
+    for (int64_t p = 0; p < P.npts; ++p) {
+      const int x = (int)(p % P.nx), y = (int)((p / P.nx) % P.ny), z = (int)(p / ((int64_t)P.nx * P.ny));
+      const int u = node_of[p], lp = lpos[p];
+      for (int o = 0; o < 27; ++o) {
+        const int qx = x + o % 3 - 1, qy = y + (o / 3) % 3 - 1, qz = z + o / 9 - 1;
+        if (qx < 0 || qx >= P.nx || qy < 0 || qy >= P.ny || qz < 0 || qz >= P.nz) continue;
+        const int64_t q = qx + (int64_t)P.nx * (qy + (int64_t)P.ny * qz);
+        const int v = node_of[q], lq = lpos[q];
+        if (u == v) {
+          P.asm_map[p * 27 + o] = lay.dg_off[u] + 3 * lp + (int64_t)3 * lq * m1[u];
+        } else if (u < v) {
+          const int col = lay.col_of(u, v);
+          if (col < 0) { err = "internal: missing level-1 block"; return SGF_ERR_INVALID_ARG; }
+          P.asm_map[p * 27 + o] = lay.dg_size + lay.up_off[u] + (int64_t)(col + 3 * lq) * m1[u] + 3 * lp;
+        }
+      }
+    }
+    P.asm_ld.assign(P.npts, 0);
+    for (int64_t p = 0; p < P.npts; ++p) P.asm_ld[p] = m1[node_of[p]];
+    q1_element_stiffness(P.nu, P.kref);
+  } else {
     const LevelSym& L1 = P.lev[0];
     std::vector<int> m1(L1.nnodes);
     for (int i = 0; i < L1.nnodes; ++i) m1[i] = (L1.pt_ptr[i + 1] - L1.pt_ptr[i]) * P.dof;

@@ -137,6 +137,8 @@ void check_block(const void* p, int64_t M, int64_t N, int64_t ld, size_t es, con
 Plan::~Plan() {
   if (cache.map) dev_free(cache.map);
   if (cache.perm) dev_free(cache.perm);
+  if (cache.ld) dev_free(cache.ld);
+  if (cache.kref) dev_free(cache.kref);
   for (int t = 0; t < 2; ++t) {
     if (cache.phi1[t]) dev_free(cache.phi1[t]);
     for (void* p : cache.reexp[t])

@@ -473,13 +473,15 @@ class FactorImpl final : public FactorBase {
     }
   }
   void spmv(const double* x, double* y, cudaStream_t s) override {
-    launch_spmv_stencil(sd_, sx_, sy_, sz_, plan->nx, plan->ny, plan->nz, x, y, s);
+    if (bsr_) launch_spmv_bsr27(bsr_, plan->nx, plan->ny, plan->nz, x, y, s);
+    else launch_spmv_stencil(sd_, sx_, sy_, sz_, plan->nx, plan->ny, plan->nz, x, y, s);
   }
 
  private:
   std::vector<void*> keep_;
   DevStatus* st_ = nullptr;
   double *sd_ = nullptr, *sx_ = nullptr, *sy_ = nullptr, *sz_ = nullptr;
+  double* bsr_ = nullptr;   // Q1 elasticity: 27 FP64 3x3 blocks per point
   const int64_t* perm1_ = nullptr;
   std::vector<LevelRec<T>> lev_;
   int mtop_ = 0;
@@ -554,6 +556,8 @@ class FactorImpl final : public FactorBase {
   struct PlanData {
     const int64_t* map;
     const int64_t* perm;
+    const int* ld;
+    const double* kref;
     const T* phi1;
     std::vector<const T*> reexp;
   };
@@ -571,6 +575,13 @@ class FactorImpl final : public FactorBase {
       dev_h2d(C.map, P.asm_map.data(), P.asm_map.size() * 8, s);
       C.perm = (int64_t*)dev_malloc(std::max<size_t>(P.perm1.size(), 1) * 8);
       dev_h2d(C.perm, P.perm1.data(), P.perm1.size() * 8, s);
+      if (!P.kref.empty()) {
+        C.ld = (int*)dev_malloc(std::max<size_t>(P.asm_ld.size(), 1) * 4);
+        dev_h2d(C.ld, P.asm_ld.data(), P.asm_ld.size() * 4, s);
+        C.kref = (double*)dev_malloc(P.kref.size() * 8);
+        dev_h2d(C.kref, P.kref.data(), P.kref.size() * 8, s);
+      }
+      dev_sync(s);
     }
     if (!C.phi1[ti]) {
       std::vector<T> h(P.phi1.size());
@@ -590,6 +601,8 @@ class FactorImpl final : public FactorBase {
     PlanData d;
     d.map = C.map;
     d.perm = C.perm;
+    d.ld = C.ld;
+    d.kref = C.kref;
     d.phi1 = (const T*)C.phi1[ti];
     for (void* p : C.reexp[ti]) d.reexp.push_back((const T*)p);
     return d;
@@ -620,18 +633,21 @@ class FactorImpl final : public FactorBase {
     build_layout(L1, m, lay);
     T* Dg = dalloc<T>(keep_, lay.dg_size, s);
     T* Up = dalloc<T>(keep_, lay.up_size, s);
-    sd_ = dalloc<double>(keep_, P.npts, s);
-    sx_ = dalloc<double>(keep_, P.npts, s);
-    sy_ = dalloc<double>(keep_, P.npts, s);
-    sz_ = dalloc<double>(keep_, P.npts, s);
     const PlanData pd = plan_data(P, s);
     perm1_ = pd.perm;
-    {
+    if (P.stencil == SGF_STENCIL_Q1_ELASTIC_3D) {
+      bsr_ = dalloc<double>(keep_, (size_t)P.npts * 27 * 9, s, false);
+      launch_assemble_q1<T>(coeffs, pd.kref, P.nx, P.ny, P.nz, pd.map, pd.ld, lay.dg_size, Dg, Up, bsr_, s);
+    } else {
+      sd_ = dalloc<double>(keep_, P.npts, s);
+      sx_ = dalloc<double>(keep_, P.npts, s);
+      sy_ = dalloc<double>(keep_, P.npts, s);
+      sz_ = dalloc<double>(keep_, P.npts, s);
       const double w = P.stencil == SGF_STENCIL_7PT_FV_3D ? 2.0 : 1.0;
       launch_assemble_scalar<T>(coeffs, P.nx, P.ny, P.nz, P.grid.dirichlet, w, pd.map, lay.dg_size, Dg, Up,
                                 sd_, sx_, sy_, sz_, s);
-      if (!dry_run()) SGF_CK(cudaGetLastError());
     }
+    if (!dry_run()) SGF_CK(cudaGetLastError());
     trace(s, 1, "assembly");
     // level-1 Phi: a working copy (merges write the next level's)
     T* Phi = nullptr;

@@ -712,6 +712,75 @@ __global__ void k_assemble(const double* __restrict__ coef, int nx, int ny, int 
   }
 }
 
+// Q1 elasticity (Sec. 7.1.3 on hexahedra): the 3x3 block between point p and
+// its neighbour at offset o sums E_e * Kref over the (up to 8) elements that
+// contain both nodes, in (ez, ey, ex) order.  Point x index i is node x = i + 1
+// (the clamped x = 0 nodes are removed); elements ex x ey x ez with
+// ex = nx, ey = ny - 1, ez = nz - 1.
+template <typename T>
+__global__ void k_assemble_q1(const double* __restrict__ E, const double* __restrict__ kref, int nx,
+                              int ny, int nz, const int64_t* __restrict__ map, const int* __restrict__ ld,
+                              int64_t dgsz, T* dg, T* up, double* __restrict__ bsr) {
+  const int64_t npts = (int64_t)nx * ny * nz;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= npts * 27) return;
+  const int64_t p = id / 27;
+  const int o = (int)(id % 27);
+  const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = (int)(p / ((int64_t)nx * ny));
+  const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+  double blk[9];
+  for (int k = 0; k < 9; ++k) blk[k] = 0.0;
+  const int qx = x + dx, qy = y + dy, qz = z + dz;
+  const bool inside = qx >= 0 && qx < nx && qy >= 0 && qy < ny && qz >= 0 && qz < nz;
+  if (inside) {
+    const int EX = nx, EY = ny - 1, EZ = nz - 1;
+    const int X = x + 1, QX = qx + 1;
+    for (int ez = max(z, qz) - 1; ez <= min(z, qz); ++ez) {
+      if (ez < 0 || ez >= EZ) continue;
+      for (int ey = max(y, qy) - 1; ey <= min(y, qy); ++ey) {
+        if (ey < 0 || ey >= EY) continue;
+        for (int ex = max(X, QX) - 1; ex <= min(X, QX); ++ex) {
+          if (ex < 0 || ex >= EX) continue;
+          const double e = E[ex + (int64_t)EX * (ey + (int64_t)EY * ez)];
+          const int ap = (X - ex) + 2 * (y - ey) + 4 * (z - ez);
+          const int aq = (QX - ex) + 2 * (qy - ey) + 4 * (qz - ez);
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) blk[3 * i + j] += e * kref[(3 * ap + i) * 24 + 3 * aq + j];
+        }
+      }
+    }
+  }
+  for (int k = 0; k < 9; ++k) bsr[id * 9 + k] = blk[k];
+  const int64_t base = map[id];
+  if (base >= 0) {
+    const int m = ld[p];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const int64_t off = base + i + (int64_t)j * m;
+        const T v = (T)blk[3 * i + j];
+        if (off < dgsz) dg[off] = v; else up[off - dgsz] = v;
+      }
+  }
+}
+
+__global__ void k_spmv_bsr27(const double* __restrict__ bsr, int nx, int ny, int nz,
+                             const double* __restrict__ x, double* __restrict__ yv) {
+  const int64_t npts = (int64_t)nx * ny * nz;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const int px = (int)(p % nx), py = (int)((p / nx) % ny), pz = (int)(p / ((int64_t)nx * ny));
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int o = 0; o < 27; ++o) {
+    const int qx = px + o % 3 - 1, qy = py + (o / 3) % 3 - 1, qz = pz + o / 9 - 1;
+    if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || qz < 0 || qz >= nz) continue;
+    const int64_t q = qx + (int64_t)nx * (qy + (int64_t)ny * qz);
+    const double* b = bsr + (p * 27 + o) * 9;
+    const double x0 = x[3 * q], x1 = x[3 * q + 1], x2 = x[3 * q + 2];
+    for (int i = 0; i < 3; ++i) acc[i] = fma(b[3 * i], x0, fma(b[3 * i + 1], x1, fma(b[3 * i + 2], x2, acc[i])));
+  }
+  for (int i = 0; i < 3; ++i) yv[3 * p + i] = acc[i];
+}
+
 __global__ void k_spmv(const double* __restrict__ sd, const double* __restrict__ sx,
                        const double* __restrict__ sy, const double* __restrict__ sz, int nx, int ny,
                        int nz, const double* __restrict__ x, double* __restrict__ yv) {
@@ -1015,6 +1084,27 @@ void launch_assemble_scalar(const double* coef, int nx, int ny, int nz, unsigned
   k_assemble<T><<<blocks_for(n), kThreads, 0, s>>>(coef, nx, ny, nz, dm, w, map, dgsz, dg, up, sd, sx, sy, sz);
 }
 
+template <typename T>
+void launch_assemble_q1(const double* E, const double* kref, int nx, int ny, int nz, const int64_t* map,
+                        const int* ld, int64_t dgsz, T* dg, T* up, double* bsr, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny * nz * 27;
+  if (dry_run()) {
+    check_range(map, 8 * n, "assemble_q1 map");
+    check_range(bsr, 8 * 9 * n, "assemble_q1 bsr");
+    return;
+  }
+  ProfScope ps(P_ASSEMBLE, s);
+  k_assemble_q1<T><<<blocks_for(n), kThreads, 0, s>>>(E, kref, nx, ny, nz, map, ld, dgsz, dg, up, bsr);
+}
+
+void launch_spmv_bsr27(const double* bsr, int nx, int ny, int nz, const double* x, double* y, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  if (dry_run()) return;
+  prof_work(2.0 * 243 * n, (243.0 * 8 + 48) * n);
+  ProfScope ps(P_SPMV, s);
+  k_spmv_bsr27<<<blocks_for(n), kThreads, 0, s>>>(bsr, nx, ny, nz, x, y);
+}
+
 void launch_spmv_stencil(const double* sd, const double* sx, const double* sy, const double* sz,
                          int nx, int ny, int nz, const double* x, double* y, cudaStream_t s) {
   const int64_t n = (int64_t)nx * ny * nz;
@@ -1106,6 +1196,9 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
   template void launch_assemble_scalar<T>(const double*, int, int, int, unsigned, double,       \
                                           const int64_t*, int64_t, T*, T*, double*, double*,    \
                                           double*, double*, cudaStream_t);                       \
+  template void launch_assemble_q1<T>(const double*, const double*, int, int, int,              \
+                                      const int64_t*, const int*, int64_t, T*, T*, double*,      \
+                                      cudaStream_t);                                             \
   template void launch_gather<T>(const double*, const int64_t*, T*, int64_t, int, int,          \
                                  cudaStream_t);                                                  \
   template void launch_scatter<T>(const T*, const int64_t*, double*, int64_t, int, int,         \

@@ -49,6 +49,14 @@ void launch_assemble_scalar(const double* coef, int nx, int ny, int nz, unsigned
                             double bweight, const int64_t* map, int64_t dg_size, T* dg, T* up,
                             double* sd, double* sx, double* sy, double* sz, cudaStream_t s);
 
+// Q1 elasticity: level-1 3x3 blocks through the 27-per-point map (ld[p] =
+// size of p's level-1 node) and the FP64 27-block BSR copy for the SpMV.
+template <typename T>
+void launch_assemble_q1(const double* E, const double* kref, int nx, int ny, int nz, const int64_t* map,
+                        const int* ld, int64_t dg_size, T* dg, T* up, double* bsr, cudaStream_t s);
+void launch_spmv_bsr27(const double* bsr, int nx, int ny, int nz, const double* x, double* y,
+                       cudaStream_t s);
+
 // y = A x for the assembled 5/7-point operator, FP64.
 void launch_spmv_stencil(const double* sd, const double* sx, const double* sy, const double* sz,
                          int nx, int ny, int nz, const double* x, double* y, cudaStream_t s);

@@ -52,6 +52,8 @@ struct Plan {
   int dof = 1;
   int pi = 1;                      // basis columns
   double tau = 1e-12;
+  double nu = 0.3;                 // Poisson ratio (Q1 elasticity)
+  std::vector<double> kref;        // Q1 element stiffness for E = 1 (24 x 24, row-major)
   std::vector<LevelSym> lev;
   // level-1 basis rows Phi (m x pi, col-major) per node, concatenated
   std::vector<double> phi1;
@@ -60,14 +62,19 @@ struct Plan {
   std::vector<std::vector<int>> mcap;
   // level-1 assembly: per point 7 destinations (x-, x+, y-, y+, z-, z+, diag)
   // in the concatenation [diagonal blocks | upper panels] of the level-1
-  // layout (-1 = not stored), and the natural DOF of each level-1 vector slot
+  // layout (-1 = not stored) - for Q1 elasticity 27 per point, the (0, 0)
+  // entry of each 3x3 neighbour block - and the natural DOF of each level-1
+  // vector slot
   std::vector<int64_t> asm_map, perm1;
+  std::vector<int> asm_ld;         // Q1: level-1 node size of every point
 
   // device copies of the plan's constant data, built on first use
   struct DevCache {
     int device = -1;
     int64_t* map = nullptr;
     int64_t* perm = nullptr;
+    int* ld = nullptr;
+    double* kref = nullptr;
     void* phi1[2] = {nullptr, nullptr};          // [double, float]
     std::vector<void*> reexp[2];                 // per level, [double, float]
   };

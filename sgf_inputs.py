@@ -172,4 +172,13 @@ def config(name: str, seed: int = 0) -> dict:
         return dict(name=name, dim=3, n=(e, e, e), stencil=STENCIL_7PT_3D,
                     dirichlet=ALL_FACES_3D, coeffs=unit_field(shape),
                     leaf=8, degree=2, basis="poly", dof=1)
+    if name.startswith("elastic_"):
+        # Q1 hexahedra on an e^3 element cube, x = 0 face clamped: the free
+        # nodes form an e x (e+1) x (e+1) point grid with 3 DOFs each;
+        # E = 1 with 8 seeded spherical inclusions of E = 1e3 (radius e/8), nu = 0.3
+        e = int(name.split("_")[1])
+        return dict(name=name, dim=3, n=(e, e + 1, e + 1), elems=(e, e, e),
+                    stencil=STENCIL_Q1_ELASTIC_3D, dirichlet=FACE_XM,
+                    coeffs=inclusion_moduli((e, e, e), 8, e / 8.0, 1.0, 1e3, seed),
+                    nu=0.3, leaf=8 if e >= 32 else 4, degree=1, basis="rbm", dof=3)
     raise KeyError(name)

@@ -38,13 +38,18 @@ CASES = [
     ((37, 29, 23), 3, 8, "7pt_fv_3d"),
     ((64, 64, 64), 3, 8, "7pt_fv_3d"),
     ((7, 7, 7), 3, 8, "7pt_3d"),
+    ((12, 13, 13), 3, 4, "q1_elastic_3d"),
 ]
 
 
 @pytest.mark.parametrize("n,dim,b,st", CASES)
 def test_symbolic_analysis_bit_exact(n, dim, b, st):
-    H = build_hierarchy(n, dim, b, st)
-    P = sgf.Plan(n, dim, st, 1, b, 2 if dim == 3 else 1)
+    elastic = st == "q1_elastic_3d"
+    H = build_hierarchy(n, dim, b, st, dof=3 if elastic else 1)
+    if elastic:
+        P = sgf.Plan(n, dim, st, 1, b, 1, basis=1, dof=3)
+    else:
+        P = sgf.Plan(n, dim, st, 1, b, 2 if dim == 3 else 1)
     assert P.nlevels == len(H.levels)
     for li, lev in enumerate(H.levels):
         ex = P.export_level(li)

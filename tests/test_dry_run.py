@@ -24,7 +24,9 @@ from paper_1907_03406_gb300 import _lib
 lib = _lib.load()
 out = []
 for (n, dim, st, dm, leaf, deg, prec, scheme) in json.loads(sys.argv[1]):
-    P = sgf.Plan(tuple(n), dim, st, dm, leaf, deg, precision=prec, scheme=scheme)
+    el = st == "q1_elastic_3d"
+    P = sgf.Plan(tuple(n), dim, st, dm, leaf, deg, precision=prec, scheme=scheme,
+                 basis=1 if el else 0, dof=3 if el else 1)
     lib.sgf_dry_run_violations(1)
     h = C.c_void_p()
     rc = lib.sgf_factor(P.handle, C.c_void_p(4096), None, C.byref(h))
@@ -51,6 +53,8 @@ CASES = [
     [[21, 18, 13], 3, "7pt_fv_3d", 1, 4, 1, "fp64", "none"],
     [[7, 7, 7], 3, "7pt_3d", 63, 8, 2, "fp64", "nest_all_all"],
     [[130, 67, 1], 2, "5pt_2d", 15, 8, 2, "mixed", "nest_all_all"],
+    [[12, 13, 13], 3, "q1_elastic_3d", 1, 4, 1, "fp64", "nest_all_all"],
+    [[24, 25, 25], 3, "q1_elastic_3d", 1, 8, 1, "mixed", "nest_all_all"],
 ]
 
 

@@ -59,8 +59,9 @@ def _oracle(cfg, scheme="nest_all_all"):
     key = (cfg["name"], scheme)
     if key not in _ORACLE_CACHE:
         A = assemble(cfg)
-        H = build_hierarchy(cfg["n"], cfg["dim"], cfg["leaf"], cfg["stencil"])
-        F = factorize(A, H, Options(scheme=scheme, degree=cfg["degree"], order="level"))
+        H = build_hierarchy(cfg["n"], cfg["dim"], cfg["leaf"], cfg["stencil"], dof=cfg.get("dof", 1))
+        F = factorize(A, H, Options(scheme=scheme, degree=cfg["degree"], order="level",
+                                    basis=cfg.get("basis", "poly")))
         _ORACLE_CACHE[key] = (A, H, F)
     return _ORACLE_CACHE[key]
 
@@ -72,7 +73,7 @@ def _tolerance(cfg, v):
     sa = sm = 0.0
     for seed in range(3):
         P = factorize(A, H, Options(degree=cfg["degree"], order="level", qr_noise=4 * 2.2e-16,
-                                    qr_noise_seed=seed))
+                                    qr_noise_seed=seed, basis=cfg.get("basis", "poly")))
         sa = max(sa, np.linalg.norm(P.solve(v) - a) / np.linalg.norm(a))
         sm = max(sm, np.linalg.norm(P.multiply(v) - m) / np.linalg.norm(m))
     return max(1e-10, 4 * sa), max(1e-10, 4 * sm)
@@ -89,7 +90,7 @@ def _t(x):
 
 
 SMALL = ["poisson2d_64", "rand2d_29_23_4", "grf3d_16", "rand3d_21_18_13_4", "grf3d_24",
-         "twophase3d_24", "grf3d_32"]
+         "twophase3d_24", "grf3d_32", "elastic_8", "elastic_12"]
 
 
 @pytest.mark.parametrize("name", SMALL)
@@ -135,7 +136,7 @@ def test_apply_and_forward_match_oracle(name):
         assert np.linalg.norm(z - zo) <= tm * np.linalg.norm(zo)
 
 
-@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "twophase3d_24"])
+@pytest.mark.parametrize("name", ["poisson2d_64", "grf3d_24", "twophase3d_24", "elastic_12"])
 def test_pcg_iterations_match_oracle(name):
     cfg = _problem(name)
     A, H, O = _oracle(cfg)
@@ -241,3 +242,24 @@ def test_multi_rhs_apply_and_block_pcg_equal_single_rhs(precision):
     for j in range(5):
         x1, info1 = F.pcg(_t(B[j]), rtol=1e-10, maxit=500)
         assert np.array_equal(x[j], x1.cpu().numpy())
+
+
+@pytest.mark.parametrize("name,precision", [("elastic_16", "fp64"), ("elastic_48", "mixed")])
+def test_rigid_body_modes_preserved_on_gpu(name, precision):
+    # Sec. 7.2: with the rigid-body basis A_l reproduces A on the six modes
+    from oracle.basis import eval_rbm
+    cfg = _problem(name)
+    plan, F = _gpu(cfg, precision=precision)
+    nx, ny, nz = cfg["n"]
+    p = np.arange(nx * ny * nz)
+    xyz = np.stack([p % nx + 1, (p // nx) % ny, p // (nx * ny)], 1).astype(float)
+    R = eval_rbm(xyz, (np.array([nx / 2, ny / 2, nz / 2]), float(max(nx, ny, nz))))
+    tol = 1e-11 if precision == "fp64" else 1e-4   # mixed: tau = 1e-6 truncation + FP32
+    for k in range(6):
+        v = _t(R[:, k])
+        a = F.apply_forward(v)
+        b = F.spmv(v)
+        assert torch.linalg.norm(a - b).item() <= tol * torch.linalg.norm(b).item()
+    bvec = _t(si.rhs(plan.n, 0))
+    x, info = F.pcg(bvec, rtol=1e-10, maxit=1000)
+    assert info["rel_residual"] <= 1e-10
