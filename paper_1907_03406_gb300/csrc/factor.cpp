@@ -1264,8 +1264,21 @@ class FactorImpl final : public FactorBase {
 
 }  // namespace
 
+// Precision policy: the mixed path factors in FP32; if an FP32 pivot is not
+// positive (or not finite) the whole problem is factored again in FP64, so a
+// matrix that is SPD but too ill-conditioned for single precision still gets
+// a factor; a genuinely non-SPD matrix fails in FP64 as well.
 std::unique_ptr<FactorBase> make_factor(const Plan& plan, const double* coeffs, cudaStream_t s) {
-  if (plan.opts.precision == SGF_PREC_MIXED) return std::make_unique<FactorImpl<float>>(plan, coeffs, s);
+  if (plan.opts.precision == SGF_PREC_MIXED) {
+    try {
+      return std::make_unique<FactorImpl<float>>(plan, coeffs, s);
+    } catch (const SgfError& e) {
+      if (e.code != SGF_ERR_NOT_SPD && e.code != SGF_ERR_NONFINITE) throw;
+    }
+    auto f = std::make_unique<FactorImpl<double>>(plan, coeffs, s);
+    f->fp64_fallback = true;
+    return f;
+  }
   return std::make_unique<FactorImpl<double>>(plan, coeffs, s);
 }
 

@@ -77,6 +77,7 @@ class FactorBase {
   const Plan* plan = nullptr;
   std::vector<LevelStats> stats;
   int bad_level = -1, bad_node = -1, status = 0;
+  bool fp64_fallback = false;   // mixed request factored in FP64 (see make_factor)
   int64_t n = 0;
 };
 

@@ -1,0 +1,54 @@
+"""Failure detection through status codes (no GPU fault is ever provoked):
+a non-SPD coefficient field gives SGF_ERR_NOT_SPD with the failing node, a
+NaN coefficient SGF_ERR_NONFINITE, too few PCG iterations
+SGF_ERR_NO_CONVERGENCE; the device keeps working afterwards."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1907_03406_gb300 as sgf  # noqa: E402
+import sgf_inputs as si  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _coeffs(k):
+    return torch.tensor(np.ascontiguousarray(k).ravel(), dtype=torch.float64, device=DEV)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_negative_coefficient_reports_not_spd(precision):
+    cfg = si.config("grf3d_16")
+    k = cfg["coeffs"].copy()
+    k[3:5, 3:5, 3:5] = -1e6           # negative diagonal entries: not positive definite
+    plan = sgf.Plan.from_config(cfg, precision=precision)
+    with pytest.raises(sgf.SGFError) as e:
+        sgf.Factor(plan, _coeffs(k))
+    assert e.value.code == -2   # SGF_ERR_NOT_SPD
+    # the context is still healthy: a valid factorization works
+    F = sgf.Factor(plan, _coeffs(cfg["coeffs"]))
+    x, info = F.pcg(torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=DEV))
+    assert info["rel_residual"] <= 1e-10
+
+
+def test_nan_coefficient_reports_nonfinite():
+    cfg = si.config("grf3d_16")
+    k = cfg["coeffs"].copy()
+    k[2, 2, 2] = np.nan
+    plan = sgf.Plan.from_config(cfg)
+    with pytest.raises(sgf.SGFError) as e:
+        sgf.Factor(plan, _coeffs(k))
+    assert e.value.code in (-2, -3)
+
+
+def test_maxit_reports_no_convergence():
+    cfg = si.config("grf3d_16")
+    plan = sgf.Plan.from_config(cfg)
+    F = sgf.Factor(plan, _coeffs(cfg["coeffs"]))
+    b = torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=DEV)
+    x, info = F.pcg(b, rtol=1e-10, maxit=2, check=False)
+    assert info["status"] == -5 and info["iterations"] == 2
