@@ -518,7 +518,8 @@ class FactorImpl final : public FactorBase {
       bad_level = h.level;
       bad_node = h.node;
       status = h.code;
-      throw SgfError(h.code, "device factorization failed (non-positive or non-finite pivot)");
+      throw SgfError(h.code, "non-positive or non-finite pivot at level " + std::to_string(h.level) +
+                                 ", node " + std::to_string(h.node));
     }
   }
 
