@@ -349,7 +349,15 @@ struct Program {
   std::vector<Acct> acct;      // launch accounting added per replay
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
+  std::vector<void*> mem;      // split-GEMV partial sums and counters
 };
+
+// Element budget of one GEMV task (one CTA): the launch's elements spread
+// over about eight CTAs per SM, kept between 4K and 32K elements (small
+// launches get more, shorter tasks; large ones long enough to hide the
+// start-up latency).
+constexpr double kGemvCtas = 152.0 * 8.0;
+constexpr double kGemvMinElems = 4096.0, kGemvMaxElems = 32768.0;
 
 template <typename T>
 struct GemvList {
@@ -367,17 +375,19 @@ struct GemvList {
     bool tri;
     T alpha;
   };
-  // y[M] = beta y + sum alpha op(A)(x - x2); op N chunks of 64 rows, op T of 32 columns
+  // y[M] = beta y + sum alpha op(A)(x - x2); op N chunks of kGemvBand rows,
+  // op T chunks of kGemvCols columns (one unsplit task each until emit)
   void add(T* y, int M, int beta, const std::vector<In>& ins) {
     if (M <= 0) return;
-    const int chunk = trans ? 32 : 64;
+    const int chunk = trans ? kGemvCols : kGemvBand;
     for (int i0 = 0; i0 < M; i0 += chunk) {
-      GemvTask<T> g;
+      GemvTask<T> g{};
       g.y = y + (size_t)i0 * nr;
       g.M = std::min(chunk, M - i0);
       g.c_begin = (int)c.size();
       g.beta = beta;
-      int cnt = 0;
+      g.nsplit = 1;
+      int cnt = 0, total = 0;
       for (const auto& in : ins) {
         if (in.K <= 0) continue;
         GemvContrib<T> q;
@@ -388,18 +398,85 @@ struct GemvList {
         q.K = in.K;
         q.tri = in.tri ? i0 + 1 : 0;
         q.alpha = in.alpha;
+        int kb, ke;
+        gemv_useful(trans, q.tri, q.K, g.M, &kb, &ke);
+        total += ke - kb;
         c.push_back(q);
         ++cnt;
       }
       g.c_count = cnt;
+      g.k_hi = total;
       t.push_back(g);
     }
   }
-  void emit(Program<T>& P) {
+
+  // Split chunks into tasks of about `budget` elements (and at most kGemvMaxC
+  // contributions each); returns the number of partial elements and counters
+  // the split chunks need.  Depends on the shapes only, not on nr.
+  void split(double budget, std::vector<GemvTask<T>>& out, size_t& npart, int& ncnt) const {
+    npart = 0;
+    ncnt = 0;
+    std::vector<int> pre;
+    for (const GemvTask<T>& g : t) {
+      pre.assign(1, 0);
+      for (int k = 0; k < g.c_count; ++k) {
+        const GemvContrib<T>& q = c[g.c_begin + k];
+        int kb, ke;
+        gemv_useful(trans, q.tri, q.K, g.M, &kb, &ke);
+        pre.push_back(pre.back() + ke - kb);
+      }
+      const int total = pre.back();
+      if (total == 0) {          // nothing to add: y = beta y
+        GemvTask<T> h = g;
+        h.c_count = 0;
+        h.k_lo = h.k_hi = 0;
+        out.push_back(h);
+        continue;
+      }
+      const int span = std::max(1, (int)(budget / g.M));
+      const int npieces = std::max(1, (total + span - 1) / span);
+      if (npieces == 1 && g.c_count <= kGemvMaxC) {
+        out.push_back(g);
+        continue;
+      }
+      const int len = (total + npieces - 1) / npieces;
+      const size_t first = out.size();
+      int cf = 0;
+      for (int a = 0; a < total;) {
+        while (pre[cf + 1] <= a) ++cf;
+        const int b = std::min({total, a + len, pre[std::min(cf + kGemvMaxC, g.c_count)]});
+        int cl = cf;
+        while (pre[cl + 1] < b) ++cl;
+        GemvTask<T> h = g;
+        h.c_begin = g.c_begin + cf;
+        h.c_count = cl - cf + 1;
+        h.k_lo = a - pre[cf];
+        h.k_hi = b - pre[cf];
+        out.push_back(h);
+        a = b;
+      }
+      const int ns = (int)(out.size() - first);
+      for (int k = 0; k < ns; ++k) {
+        GemvTask<T>& h = out[first + k];
+        h.split = k;
+        h.nsplit = ns;
+        // offsets for now; made pointers once the buffers exist
+        h.part = (T*)(uintptr_t)(npart * sizeof(T));
+        h.cnt = (int*)(uintptr_t)((size_t)ncnt * sizeof(int));
+      }
+      if (ns > 1) {
+        npart += (size_t)ns * g.M * nr;
+        ++ncnt;
+      }
+    }
+  }
+
+  template <class Prog>
+  void emit(Prog& P, cudaStream_t s) {
     if (t.empty()) return;
-    double fl = 0, by = 0;
+    double fl = 0, by = 0, el_all = 0;
     for (const auto& g : t) {
-      by += (double)sizeof(T) * g.M * (g.beta ? 2 : 1);
+      by += (double)sizeof(T) * g.M * nr * (g.beta ? 2 : 1);
       for (int k = g.c_begin; k < g.c_begin + g.c_count; ++k) {
         // elements of A read: the lower-triangular ones only when tri is set
         double el = (double)g.M * c[k].K;
@@ -409,18 +486,44 @@ struct GemvList {
                      : 0.5 * ((hi) * (hi + 1) - lo * (lo + 1));
         }
         fl += 2.0 * el;
-        by += (double)sizeof(T) * (el + c[k].K * (c[k].x2 ? 2.0 : 1.0));
+        el_all += el;
+        by += (double)sizeof(T) * (el + (double)c[k].K * nr * (c[k].x2 ? 2.0 : 1.0));
       }
     }
-    const size_t ot = P.b.push(t), oc = P.b.push(c);
-    const int n = (int)t.size();
+    const double budget = std::min(kGemvMaxElems, std::max(kGemvMinElems, el_all / kGemvCtas));
+    std::vector<GemvTask<T>> tasks;
+    size_t npart = 0;
+    int ncnt = 0;
+    split(budget, tasks, npart, ncnt);
+    T* part = nullptr;
+    int* cnt = nullptr;
+    if (ncnt > 0) {
+      part = (T*)dev_malloc(npart * sizeof(T));
+      cnt = (int*)dev_malloc((size_t)ncnt * sizeof(int));
+      dev_memset(cnt, 0, (size_t)ncnt * sizeof(int), s);
+      P.mem.push_back(part);
+      P.mem.push_back(cnt);
+    }
+    for (auto& h : tasks) {
+      if (h.nsplit > 1) {
+        h.part = part + (uintptr_t)h.part / sizeof(T);
+        h.cnt = cnt + (uintptr_t)h.cnt / sizeof(int);
+      } else {
+        h.part = nullptr;
+        h.cnt = nullptr;
+      }
+    }
+    const size_t ot = P.b.push(tasks), oc = P.b.push(c);
+    const int n = (int)tasks.size();
     const bool tr = trans;
     const int r = nr;
+    int max_m = 1;
+    for (const auto& h : tasks) max_m = std::max(max_m, h.M);
     P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl * r, by});
-    P.ops.push_back([=](const char* d, cudaStream_t s) {
+    P.ops.push_back([=](const char* d, cudaStream_t st) {
       prof_work(fl * r, by);
-      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, s);
-      else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, s);
+      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, st);
+      else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, max_m, st);
     });
     t.clear();
     c.clear();
@@ -504,6 +607,8 @@ class FactorImpl final : public FactorBase {
           if (P->exec) cudaGraphExecDestroy(P->exec);
           if (P->graph) cudaGraphDestroy(P->graph);
         }
+        for (void* m : P->mem) dev_free(m);
+        P->mem.clear();
         P->b.dev = nullptr;
         P->exec = nullptr;
         P->graph = nullptr;
@@ -1070,8 +1175,8 @@ class FactorImpl final : public FactorBase {
     const int k = nr == 1 ? 0 : nr == 2 ? 1 : nr == 4 ? 2 : 3;
     Program<T>& P = inverse ? inv_[k] : fwd_[k];
     if (P.ops.empty()) {
-      if (inverse) build_inverse(P, nr);
-      else build_forward(P, nr);
+      if (inverse) build_inverse(P, nr, s);
+      else build_forward(P, nr, s);
       P.b.upload_persistent(s);
     }
     return P;
@@ -1098,7 +1203,7 @@ class FactorImpl final : public FactorBase {
     });
   }
 
-  void build_inverse(Program<T>& P, int nr) {
+  void build_inverse(Program<T>& P, int nr, cudaStream_t s) {
     const int nl = (int)lev_.size();
     for (int t = 0; t < nl; ++t) {
       const LevelRec<T>& R = lev_[t];
@@ -1126,10 +1231,10 @@ class FactorImpl final : public FactorBase {
         f3.add(w + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
         f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
       }
-      f1.emit(P);
-      f2.emit(P);
-      f3.emit(P);
-      f4.emit(P);
+      f1.emit(P, s);
+      f2.emit(P, s);
+      f3.emit(P, s);
+      f4.emit(P, s);
       std::vector<VecCopyTask> vc;
       for (const auto& c : R.sep)
         if (c.k > 0) vc.push_back({nr * ((c.comp ? 2 * vs : 0) + lay.vec_off[c.node]), nr * c.dst, nr * c.k, 0});
@@ -1143,8 +1248,8 @@ class FactorImpl final : public FactorBase {
       bt.trans = true;
       a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1)}});
       bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
-      a.emit(P);
-      bt.emit(P);
+      a.emit(P, s);
+      bt.emit(P, s);
     }
     for (int t = nl - 1; t >= 0; --t) {
       const LevelRec<T>& R = lev_[t];
@@ -1172,16 +1277,16 @@ class FactorImpl final : public FactorBase {
         b3.add(w + nr * lay.vec_off[r.node], r.m, 1, ins);
         b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
       }
-      b1.emit(P);
-      b2.emit(P);
-      b3.emit(P);
-      b4.emit(P);
+      b1.emit(P, s);
+      b2.emit(P, s);
+      b3.emit(P, s);
+      b4.emit(P, s);
     }
   }
 
   // y = A_l x: the factors applied in the opposite order (G^T, B^T up, top
   // L L^T, then B, G down)
-  void build_forward(Program<T>& P, int nr) {
+  void build_forward(Program<T>& P, int nr, cudaStream_t s) {
     const int nl = (int)lev_.size();
     for (int t = 0; t < nl; ++t) {
       const LevelRec<T>& R = lev_[t];
@@ -1204,10 +1309,10 @@ class FactorImpl final : public FactorBase {
         c1.add(w + nr * lay.vec_off[c.node], c.m, 0, {{c.L, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
         c2.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
       }
-      a1.emit(P);
-      a2.emit(P);
-      c1.emit(P);
-      c2.emit(P);
+      a1.emit(P, s);
+      a2.emit(P, s);
+      c1.emit(P, s);
+      c2.emit(P, s);
       std::vector<VecCopyTask> vc;
       for (const auto& c : R.sep)
         if (c.k > 0) vc.push_back({nr * ((c.comp ? 2 * vs : 0) + lay.vec_off[c.node]), nr * c.dst, nr * c.k, 0});
@@ -1220,8 +1325,8 @@ class FactorImpl final : public FactorBase {
       a.trans = true;
       a.add(w, mtop_, 0, {{Ltop_, mtop_, v, nullptr, mtop_, true, T(1)}});
       bn.add(v, mtop_, 0, {{Ltop_, mtop_, w, nullptr, mtop_, true, T(1)}});
-      a.emit(P);
-      bn.emit(P);
+      a.emit(P, s);
+      bn.emit(P, s);
     }
     for (int t = nl - 1; t >= 0; --t) {
       const LevelRec<T>& R = lev_[t];
@@ -1255,10 +1360,10 @@ class FactorImpl final : public FactorBase {
       }
       for (const auto& r : R.in)
         b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.L, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
-      b1.emit(P);
-      b2.emit(P);
-      b3.emit(P);
-      b4.emit(P);
+      b1.emit(P, s);
+      b2.emit(P, s);
+      b3.emit(P, s);
+      b4.emit(P, s);
     }
   }
 };

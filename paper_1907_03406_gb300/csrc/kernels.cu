@@ -575,92 +575,260 @@ __global__ void __launch_bounds__(kThreads) k_qrcp(const QrTask<T>* __restrict__
 // ---------------------------------------------------------------------------
 // batched GEMV
 // ---------------------------------------------------------------------------
-// op(A) = A: chunk of <= 64 output rows; 4 groups of 64 threads split the
-// columns.  NR right-hand sides are interleaved (element i of RHS q at
-// i * NR + q), so each matrix entry is read once for all of them.
-template <typename T, int NR>
-__global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restrict__ tasks,
-                                                     const GemvContrib<T>* __restrict__ cons) {
-  const GemvTask<T> tk = tasks[blockIdx.x];
-  const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
-  T acc[NR];
-#pragma unroll
-  for (int q = 0; q < NR; ++q) acc[q] = T(0);
-  if (r < tk.M) {
-    for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
-      const GemvContrib<T> cb = cons[c];
-      int kend = cb.K;
-      if (cb.tri) kend = min(kend, cb.tri - 1 + r + 1);  // lower triangular: j <= row
-      const T* a = cb.A + r;
-      T part[NR];
-#pragma unroll
-      for (int q = 0; q < NR; ++q) part[q] = T(0);
-#pragma unroll 4
-      for (int j = g; j < kend; j += 4) {
-        const T av = a[(size_t)j * cb.lda];
-#pragma unroll
-        for (int q = 0; q < NR; ++q) {
-          T xv = cb.x[(size_t)j * NR + q];
-          if (cb.x2) xv -= cb.x2[(size_t)j * NR + q];
-          part[q] = fma(av, xv, part[q]);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NR; ++q) acc[q] = fma(cb.alpha, part[q], acc[q]);
+// Contributions of a task staged in shared memory with the flat prefix of
+// their useful lengths (pre[c] .. pre[c + 1] is contribution c).
+template <typename T>
+struct GemvStage {
+  GemvContrib<T> c[kGemvMaxC];
+  int kb[kGemvMaxC];
+  int pre[kGemvMaxC + 1];
+};
+
+template <typename T>
+__device__ __forceinline__ void gemv_stage(const GemvTask<T>& tk, const GemvContrib<T>* __restrict__ cons,
+                                           bool trans, GemvStage<T>& S) {
+  const int t = threadIdx.x;
+  if (t < 32) {
+    int len = 0;
+    if (t < tk.c_count) {
+      const GemvContrib<T> c = cons[tk.c_begin + t];
+      int kb, ke;
+      gemv_useful(trans, c.tri, c.K, tk.M, &kb, &ke);
+      S.c[t] = c;
+      S.kb[t] = kb;
+      len = ke - kb;
     }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, len, o);
+      if (t >= o) len += v;
+    }
+    S.pre[t + 1] = len;
+    if (t == 0) S.pre[0] = 0;
   }
-  __shared__ T red[4][64][NR];
-#pragma unroll
-  for (int q = 0; q < NR; ++q) red[g][r][q] = acc[q];
   __syncthreads();
-  if (g == 0 && r < tk.M) {
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      const T v = (red[0][r][q] + red[1][r][q]) + (red[2][r][q] + red[3][r][q]);
-      T* y = tk.y + (size_t)r * NR + q;
-      *y = tk.beta ? *y + v : v;
-    }
+}
+
+// A task's result element e (= output * NR + rhs): written to y when the
+// chunk is not split, else to the task's partial.
+template <typename T>
+__device__ __forceinline__ void gemv_put(const GemvTask<T>& tk, int e, T v, int ne) {
+  if (tk.nsplit == 1) {
+    T* y = tk.y + e;
+    *y = tk.beta ? *y + v : v;
+  } else {
+    tk.part[(size_t)tk.split * ne + e] = v;
   }
 }
 
-// op(A) = A^T: chunk of <= 32 outputs (columns of A); one warp per output
+// Split tasks: after every partial of this task is written, the last of the
+// chunk's tasks to arrive adds the partials in split order, writes y and
+// re-arms the counter for the next launch.  Nothing waits.
+template <typename T>
+__device__ __forceinline__ void gemv_finish(const GemvTask<T>& tk, int ne) {
+  if (tk.nsplit == 1) return;
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(tk.cnt, 1) == tk.nsplit - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < ne; e += kThreads) {
+    T v = T(0);
+    for (int sp = 0; sp < tk.nsplit; ++sp) v += __ldcg(tk.part + (size_t)sp * ne + e);
+    T* y = tk.y + e;
+    *y = tk.beta ? *y + v : v;
+  }
+  if (threadIdx.x == 0) *tk.cnt = 0;
+}
+
+// Bulk prefetch of the 16-byte-aligned interior of [p, p + bytes) into L2
+// (no registers held, nothing returned; the ragged ends are left to the loads).
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = (a + 15) & ~uintptr_t(15), hi = (a + bytes) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
+// One column of an op N step: its x entries (scaled) and the band rows of the
+// current pass (zero outside the band and, for a lower-triangular block,
+// above the diagonal).
+template <typename T, int NR, int MP>
+__device__ __forceinline__ void gemv_n_col(const GemvStage<T>& S, int& c, int f, int r0, int lane, int M,
+                                           T (&av)[MP], T (&xv)[NR]) {
+  while (f >= S.pre[c + 1]) ++c;
+  const GemvContrib<T>& cb = S.c[c];
+  const int j = S.kb[c] + (f - S.pre[c]);
+  const T* col = cb.A + (size_t)j * cb.lda;
+  const int rmin = cb.tri ? j - (cb.tri - 1) : 0;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    T v = cb.x[(size_t)j * NR + q];
+    if (cb.x2) v -= cb.x2[(size_t)j * NR + q];
+    xv[q] = cb.alpha * v;
+  }
+#pragma unroll
+  for (int t = 0; t < MP; ++t) {
+    const int r = r0 + lane + 32 * t;
+    av[t] = (r < M && r >= rmin) ? col[r] : T(0);
+  }
+}
+
+// op(A) = A: a band of <= 32 * MT rows (MT = 8 or 16, chosen per launch from
+// its largest band).  The task's column segments are first prefetched into L2
+// (thread t takes flat columns t, t + 256, ...).  Warp w then takes the flat
+// columns k_lo + w, k_lo + w + 8, ..., two per step so that two columns' loads
+// are in flight; its lanes read the column's band rows (coalesced, 32
+// consecutive rows per load) into per-row accumulators, and the eight warps'
+// partial rows are added in warp order.  For NR > 1 the band is swept in
+// passes of fewer rows so the registers stay bounded; each row's sum runs
+// over the same columns in the same order for every NR.
+template <typename T, int NR, int MT>
+__global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restrict__ tasks,
+                                                     const GemvContrib<T>* __restrict__ cons) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int MP = MT / NR > 0 ? MT / NR : 1;   // 32-row groups per pass
+  // two columns per step unless that would cost too many registers (FP64, wide bands)
+  constexpr bool kTwo = sizeof(T) == 4 || MP <= 8;
+  const GemvTask<T> tk = tasks[blockIdx.x];
+  __shared__ GemvStage<T> S;
+  __shared__ T red[kWarps][32 * MP * NR];
+  gemv_stage(tk, cons, false, S);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  {
+    int c = 0;
+    for (int f = tk.k_lo + threadIdx.x; f < tk.k_hi; f += kThreads) {
+      while (f >= S.pre[c + 1]) ++c;
+      const GemvContrib<T>& cb = S.c[c];
+      const int j = S.kb[c] + (f - S.pre[c]);
+      const int rs = cb.tri ? max(0, j - (cb.tri - 1)) : 0;
+      l2_prefetch(cb.A + (size_t)j * cb.lda + rs, sizeof(T) * (size_t)(tk.M - rs));
+    }
+  }
+  for (int r0 = 0; r0 < tk.M; r0 += 32 * MP) {
+    T acc[MP][NR];
+#pragma unroll
+    for (int t = 0; t < MP; ++t)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[t][q] = T(0);
+    int c = 0;
+    for (int f = tk.k_lo + w; f < tk.k_hi; f += (kTwo ? 2 : 1) * kWarps) {
+      T av0[MP], xv0[NR], av1[MP], xv1[NR];
+      gemv_n_col<T, NR, MP>(S, c, f, r0, lane, tk.M, av0, xv0);
+      const bool two = kTwo && f + kWarps < tk.k_hi;
+      int c1 = c;
+      if (two) {
+        gemv_n_col<T, NR, MP>(S, c1, f + kWarps, r0, lane, tk.M, av1, xv1);
+      } else {
+#pragma unroll
+        for (int t = 0; t < MP; ++t) av1[t] = T(0);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) xv1[q] = T(0);
+      }
+#pragma unroll
+      for (int t = 0; t < MP; ++t)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[t][q] = fma(av0[t], xv0[q], acc[t][q]);
+      if (two) {
+#pragma unroll
+        for (int t = 0; t < MP; ++t)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[t][q] = fma(av1[t], xv1[q], acc[t][q]);
+      }
+      c = c1;
+    }
+#pragma unroll
+    for (int t = 0; t < MP; ++t)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) red[w][(lane + 32 * t) * NR + q] = acc[t][q];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * MP * NR; e += kThreads) {
+      const int r = r0 + e / NR;
+      if (r < tk.M) {
+        T v = T(0);
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) v += red[k][e];
+        gemv_put(tk, r0 * NR + e, v, tk.M * NR);
+      }
+    }
+    __syncthreads();
+  }
+  gemv_finish(tk, tk.M * NR);
+}
+
+// op(A) = A^T: <= kGemvCols outputs, column o of A handled by warp o % 8
+// (four columns per warp, their loads interleaved).  The task's column
+// segments are prefetched into L2 first; lanes then stride over the flat rows
+// of each contribution, and the lane sums are combined by a butterfly.
 template <typename T, int NR>
 __global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restrict__ tasks,
                                                      const GemvContrib<T>* __restrict__ cons) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int CW = kGemvCols / kWarps;
   const GemvTask<T> tk = tasks[blockIdx.x];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = warp; o < tk.M; o += kThreads / 32) {
-    T acc[NR];
+  __shared__ GemvStage<T> S;
+  gemv_stage(tk, cons, true, S);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // prefetch: one (contribution, column) segment per thread
+  for (int sidx = threadIdx.x; sidx < tk.c_count * tk.M; sidx += kThreads) {
+    const int c = sidx / tk.M, o = sidx - c * tk.M;
+    const int f0 = max(S.pre[c], tk.k_lo), f1 = min(S.pre[c + 1], tk.k_hi);
+    if (f0 >= f1) continue;
+    const GemvContrib<T>& cb = S.c[c];
+    int i0 = S.kb[c] + (f0 - S.pre[c]);
+    const int i1 = S.kb[c] + (f1 - S.pre[c]);
+    if (cb.tri) i0 = max(i0, cb.tri - 1 + o);
+    if (i1 > i0) l2_prefetch(cb.A + (size_t)o * cb.lda + i0, sizeof(T) * (size_t)(i1 - i0));
+  }
+  T acc[CW][NR];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) acc[q] = T(0);
-    for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
-      const GemvContrib<T> cb = cons[c];
-      const int i0 = cb.tri ? (cb.tri - 1 + o) : 0;  // lower triangular: i >= column
-      const T* a = cb.A + (size_t)o * cb.lda;
-      T part[NR];
+  for (int u = 0; u < CW; ++u)
 #pragma unroll
-      for (int q = 0; q < NR; ++q) part[q] = T(0);
-#pragma unroll 4
-      for (int i = i0 + lane; i < cb.K; i += 32) {
-        const T av = a[i];
+    for (int q = 0; q < NR; ++q) acc[u][q] = T(0);
+  if (w < tk.M) {
+    for (int c = 0; c < tk.c_count; ++c) {
+      const int f0 = max(S.pre[c], tk.k_lo), f1 = min(S.pre[c + 1], tk.k_hi);
+      if (f0 >= f1) continue;
+      const GemvContrib<T>& cb = S.c[c];
+      const int i0 = S.kb[c] + (f0 - S.pre[c]), i1 = S.kb[c] + (f1 - S.pre[c]);
+      const T* a = cb.A + (size_t)w * cb.lda;
+      const size_t cstep = (size_t)kWarps * cb.lda;
+      const int cmin = cb.tri ? cb.tri - 1 + w : 0;   // absolute column of u = 0
+#pragma unroll 2
+      for (int i = i0 + lane; i < i1; i += 32) {
+        T xv[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-          T xv = cb.x[(size_t)i * NR + q];
-          if (cb.x2) xv -= cb.x2[(size_t)i * NR + q];
-          part[q] = fma(av, xv, part[q]);
+          T v = cb.x[(size_t)i * NR + q];
+          if (cb.x2) v -= cb.x2[(size_t)i * NR + q];
+          xv[q] = cb.alpha * v;
         }
-      }
+        T av[CW];
 #pragma unroll
-      for (int q = 0; q < NR; ++q) acc[q] = fma(cb.alpha, warp_sum(part[q]), acc[q]);
-    }
-    if (lane == 0) {
+        for (int u = 0; u < CW; ++u) {
+          const int o = w + kWarps * u;
+          // lower-triangular: rows above the column's absolute index are zero
+          av[u] = (o < tk.M && (!cb.tri || i >= cmin + kWarps * u)) ? a[u * cstep + i] : T(0);
+        }
 #pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        T* y = tk.y + (size_t)o * NR + q;
-        *y = tk.beta ? *y + acc[q] : acc[q];
+        for (int u = 0; u < CW; ++u)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[u][q] = fma(av[u], xv[q], acc[u][q]);
       }
     }
   }
+#pragma unroll
+  for (int u = 0; u < CW; ++u) {
+    const int o = w + kWarps * u;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const T v = warp_sum(acc[u][q]);
+      if (lane == 0 && o < tk.M) gemv_put(tk, o * NR + q, v, tk.M * NR);
+    }
+  }
+  gemv_finish(tk, tk.M * NR);
 }
 
 template <typename T>
@@ -1015,37 +1183,59 @@ void launch_qrcp(const QrTask<T>* tasks, int n, int* ranks, double tau, int max_
 }
 
 template <typename T>
-static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, bool trans, int nr) {
+static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, bool trans, int nr,
+                       int max_m) {
   for (int i = 0; i < n; ++i) {
     const GemvTask<T>& t = tasks[i];
-    if (t.M > (trans ? 32 : 64) || t.M < 1) check_range(nullptr, 1, "gemv chunk shape");
+    if (t.M > (trans ? kGemvCols : kGemvBand) || t.M < 1 || t.M > max_m) check_range(nullptr, 1, "gemv chunk shape");
+    if (t.c_count < 0 || t.c_count > kGemvMaxC) check_range(nullptr, 1, "gemv contribution count");
     check_range(t.y, sizeof(T) * t.M * nr, "gemv y");
+    int total = 0;
     for (int c = t.c_begin; c < t.c_begin + t.c_count; ++c) {
       const GemvContrib<T>& q = cons[c];
       if (trans) check_block(q.A, q.K, t.M, q.lda, sizeof(T), "gemvT A");
       else check_block(q.A, t.M, q.K, q.lda, sizeof(T), "gemv A");
       check_range(q.x, sizeof(T) * q.K * nr, "gemv x");
       if (q.x2) check_range(q.x2, sizeof(T) * q.K * nr, "gemv x2");
+      int kb, ke;
+      gemv_useful(trans, q.tri, q.K, t.M, &kb, &ke);
+      total += ke - kb;
+    }
+    if (t.k_lo < 0 || t.k_hi > total || (t.k_lo >= t.k_hi && total > 0))
+      check_range(nullptr, 1, "gemv flat range");
+    if (t.nsplit > 1) {
+      if (t.split < 0 || t.split >= t.nsplit) check_range(nullptr, 1, "gemv split index");
+      check_range(t.part, sizeof(T) * (size_t)t.nsplit * t.M * nr, "gemv partials");
+      check_range(t.cnt, sizeof(int), "gemv counter");
+    } else if (t.nsplit != 1) {
+      check_range(nullptr, 1, "gemv split count");
     }
   }
 }
 
+template <typename T, int NR>
+static void gemv_n_mt(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int max_m, cudaStream_t s) {
+  if (max_m <= 256) k_gemv_n<T, NR, 8><<<n, kThreads, 0, s>>>(tasks, cons);
+  else k_gemv_n<T, NR, 16><<<n, kThreads, 0, s>>>(tasks, cons);
+}
+
 template <typename T>
-void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, false, nr);
+void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, int max_m,
+                   cudaStream_t s) {
+  if (dry_run()) return check_gemv(tasks, cons, n, false, nr, max_m);
   if (n <= 0) return;
   ProfScope ps(P_GEMV_N, s);
   switch (nr) {
-    case 1: k_gemv_n<T, 1><<<n, kThreads, 0, s>>>(tasks, cons); break;
-    case 2: k_gemv_n<T, 2><<<n, kThreads, 0, s>>>(tasks, cons); break;
-    case 4: k_gemv_n<T, 4><<<n, kThreads, 0, s>>>(tasks, cons); break;
-    default: k_gemv_n<T, 8><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    case 1: gemv_n_mt<T, 1>(tasks, cons, n, max_m, s); break;
+    case 2: gemv_n_mt<T, 2>(tasks, cons, n, max_m, s); break;
+    case 4: gemv_n_mt<T, 4>(tasks, cons, n, max_m, s); break;
+    default: gemv_n_mt<T, 8>(tasks, cons, n, max_m, s); break;
   }
 }
 
 template <typename T>
 void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, true, nr);
+  if (dry_run()) return check_gemv(tasks, cons, n, true, nr, kGemvCols);
   if (n <= 0) return;
   ProfScope ps(P_GEMV_T, s);
   switch (nr) {
@@ -1188,7 +1378,7 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
   template void launch_copy<T, T>(const CopyTask<T, T>*, int, cudaStream_t);                    \
   template void launch_qrcp<T>(const QrTask<T>*, int, int*, double, int, int, long long,        \
                                cudaStream_t);                                                    \
-  template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int,           \
+  template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int, int,      \
                                  cudaStream_t);                                                  \
   template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int,           \
                                  cudaStream_t);                                                  \

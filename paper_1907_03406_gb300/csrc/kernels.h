@@ -32,8 +32,10 @@ void launch_qrcp(const QrTask<T>* tasks, int ntasks, int* ranks, double tau, int
                  long long cap_elems, cudaStream_t s);
 size_t qr_smem_bytes(int m, int c, size_t elem_size, long long cap_elems);
 // nr right-hand sides interleaved (nr in 1, 2, 4, 8)
+// max_m: largest chunk of the launch (op N bands up to 256 rows use a
+// narrower kernel)
 template <typename T>
-void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr,
+void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr, int max_m,
                    cudaStream_t s);
 template <typename T>
 void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr,

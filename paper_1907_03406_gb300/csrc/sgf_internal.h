@@ -13,6 +13,12 @@
 
 #include "sgf.h"
 
+#if defined(__CUDACC__)
+#define SGF_HD __host__ __device__
+#else
+#define SGF_HD
+#endif
+
 namespace sgf {
 
 // ---------------------------------------------------------------------------
@@ -162,10 +168,27 @@ struct QrTask {          // column-pivoted Householder QR of A (m x c, ld = m)
   int m, c, node, slot;  // slot: index of the rank output
 };
 
+// Batched GEMV.  A chunk is y[M] = beta*y + sum_c alpha_c op(A_c) (x_c - x2_c)
+// over its contributions c; op N chunks are bands of <= kGemvBand rows, op T
+// chunks hold <= kGemvCols columns of A; one CTA works on one task.  The
+// contributions' useful indices (columns for op N, rows for op T; see
+// gemv_useful) are concatenated into one flat range, and a chunk may be split
+// into nsplit pieces of that range, each a task.  A split task writes its
+// partial sums to part[split]; the last of the chunk's tasks to arrive (an
+// atomic counter) adds the partials in split order and writes y, so the
+// result does not depend on scheduling.
+constexpr int kGemvBand = 512;
+constexpr int kGemvCols = 32;
+constexpr int kGemvMaxC = 32;   // contributions per task
+
 template <typename T>
-struct GemvTask {        // y[M] = beta*y + sum_c alpha_c op(A_c) (x_c - x2_c)
+struct GemvTask {
   T* y;
+  T* part;               // nsplit > 1: [nsplit][M][nr] partial sums of the chunk
+  int* cnt;              // nsplit > 1: arrival counter, zero between launches
   int M, c_begin, c_count, beta;
+  int k_lo, k_hi;        // flat range of this task over contributions c_begin..
+  int split, nsplit;
 };
 
 template <typename T>
@@ -179,6 +202,22 @@ struct GemvContrib {
                          // chunk has absolute index t - 1: the zero half is skipped
   T alpha;
 };
+
+// Useful index range [kb, ke) of a contribution to a chunk of M outputs: all K
+// for a dense block; for a lower-triangular one the columns j <= last row (op
+// N) or the rows i >= first column (op T).
+SGF_HD inline void gemv_useful(bool trans, int tri, int K, int M, int* kb, int* ke) {
+  if (!tri) {
+    *kb = 0;
+    *ke = K;
+  } else if (trans) {
+    *kb = tri - 1 < K ? tri - 1 : K;
+    *ke = K;
+  } else {
+    *kb = 0;
+    *ke = tri - 1 + M < K ? tri - 1 + M : K;
+  }
+}
 
 struct VecCopyTask {     // dst[i] = src[i] for i < len (level-vector gathers)
   int64_t src, dst;
