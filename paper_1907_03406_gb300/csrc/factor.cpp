@@ -239,13 +239,18 @@ struct Front {
 // and of the identity (giving L^{-1}), batched over all fronts.
 template <typename T>
 void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level) {
-  // small fronts without a panel: one CTA does the whole sweep
+  // Small fronts without a panel: one CTA does the whole sweep.  Beyond
+  // kFrontSmall the tile sweep spread over many CTAs wins (one CTA pays a
+  // memory latency per tile product), and so it does for fronts above
+  // kFrontTiny when the batch holds too few of them to occupy every SM.
+  int nfit = 0;
+  for (const auto& f : Fall)
+    if (f.s == 0 && f.m <= kFrontSmall) ++nfit;
+  const int cut = nfit >= kFrontBatchMin ? kFrontSmall : kFrontTiny;
   std::vector<FrontTask<T>> small;
   std::vector<Front<T>> F;
   for (const auto& f : Fall) {
-    // beyond kFrontSmall the tile sweep spread over many CTAs wins: one CTA
-    // pays a memory latency per tile product
-    if (f.s == 0 && f.m <= kFrontSmall) small.push_back({f.D, f.Li, f.m, f.node});
+    if (f.s == 0 && f.m <= cut) small.push_back({f.D, f.Li, f.m, f.node});
     else F.push_back(f);
   }
   if (!small.empty()) {
@@ -1167,8 +1172,7 @@ class FactorImpl final : public FactorBase {
     for (int t = 0; t < nl; ++t)
       vb_[t] = dalloc<T>(keep_, 3 * (size_t)kMaxNr * std::max<int64_t>(lev_[t].lay.vec_size, 1), s);
     vtop_ = dalloc<T>(keep_, 2 * (size_t)kMaxNr * std::max(mtop_, 1), s);
-    program(true, 1, s);
-    program(false, 1, s);
+    program(true, 1, s);   // the forward (multiply) programs are built on first use
   }
 
   Program<T>& program(bool inverse, int nr, cudaStream_t s) {

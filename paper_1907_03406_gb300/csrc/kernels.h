@@ -22,6 +22,10 @@ template <typename T>
 void launch_diag(const DiagTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
 // whole blocked Cholesky + inverse of small fronts, one CTA each
 constexpr int kFrontSmall = 512;
+// fronts up to kFrontTiny always take the one-CTA kernel; larger ones only in
+// batches of at least kFrontBatchMin (about one per SM)
+constexpr int kFrontTiny = 128;
+constexpr int kFrontBatchMin = 152;
 template <typename T>
 void launch_front(const FrontTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
 template <typename S, typename D>
