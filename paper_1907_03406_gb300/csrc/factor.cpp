@@ -240,13 +240,14 @@ struct Front {
 template <typename T>
 void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level) {
   // Small fronts without a panel: one CTA does the whole sweep.  Beyond
-  // kFrontSmall the tile sweep spread over many CTAs wins (one CTA pays a
+  // front_small the tile sweep spread over many CTAs wins (one CTA pays a
   // memory latency per tile product), and so it does for fronts above
   // kFrontTiny when the batch holds too few of them to occupy every SM.
+  constexpr int small_max = front_small<T>();
   int nfit = 0;
   for (const auto& f : Fall)
-    if (f.s == 0 && f.m <= kFrontSmall) ++nfit;
-  const int cut = nfit >= kFrontBatchMin ? kFrontSmall : kFrontTiny;
+    if (f.s == 0 && f.m <= small_max) ++nfit;
+  const int cut = nfit >= kFrontBatchMin ? small_max : std::min(kFrontTiny, small_max);
   std::vector<FrontTask<T>> small;
   std::vector<Front<T>> F;
   for (const auto& f : Fall) {

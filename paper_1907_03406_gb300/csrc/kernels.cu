@@ -219,9 +219,16 @@ constexpr int kPitch = kTile + 1;
 // Cholesky of the n x n tile A (ld lda) in shared memory S, L^{-1} in V;
 // writes L (strict upper part zeroed) back to A and L^{-1} to Li.  Returns
 // 0, 1 (pivot <= 0) or 2 (non-finite pivot), the same in every thread.
+//
+// Right-looking with one barrier per column: every thread reads the pivot d_j
+// itself, the trailing update uses the unscaled column (a_ik -= a_ij a_kj /
+// d_j), and the columns are scaled by d_j^{-1/2} once at the end.  The inverse
+// is a forward substitution per column of V, each owned by four lanes of one
+// warp, so its row steps need only warp synchronisation.
 template <typename T>
 __device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
   __shared__ int bad;
+  __shared__ T dinv[kTile];   // d_j^{-1/2}
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
     const int i = e % n, j = e / n;
     S[i * kPitch + j] = A[(size_t)i + (size_t)j * lda];
@@ -229,28 +236,32 @@ __device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int mybad = 0;
   for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      T d = S[j * kPitch + j];
-      if (!(d > T(0)) || !isfinite(d)) {
-        bad = isfinite(d) ? 1 : 2;
-        d = T(1);
-      }
-      S[j * kPitch + j] = sqrt(d);
+    T d = S[j * kPitch + j];
+    if (!(d > T(0)) || !isfinite(d)) {
+      mybad = isfinite(d) ? 1 : 2;
+      d = T(1);
     }
-    __syncthreads();
-    const T dj = S[j * kPitch + j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += kThreads) S[i * kPitch + j] /= dj;
-    __syncthreads();
-    // trailing lower triangle, 16 x 16 thread grid
+    const T rd = T(1) / d;
+    // trailing lower triangle, 16 x 16 thread grid; column j itself is read only
     for (int i = j + 1 + ty; i < n; i += 16) {
-      const T lij = S[i * kPitch + j];
+      const T lij = S[i * kPitch + j] * rd;
       for (int k = j + 1 + tx; k <= i; k += 16) S[i * kPitch + k] -= lij * S[k * kPitch + j];
+    }
+    if (threadIdx.x == 0) {
+      dinv[j] = T(1) / sqrt(d);
+      if (mybad) S[j * kPitch + j] = d;   // failed pivot: continue with 1 (status reported)
     }
     __syncthreads();
   }
-  // V = L^{-1} row by row; each entry V[i][c] is a dot product split over 4
-  // neighbouring lanes
+  if (threadIdx.x == 0 && mybad) bad = mybad;
+  // scale: L_ij = a_ij d_j^{-1/2} (diagonal: sqrt(d_j))
+  for (int e = threadIdx.x; e < n * n; e += kThreads) {
+    const int i = e / n, j = e % n;
+    if (j <= i) S[i * kPitch + j] *= dinv[j];
+  }
+  __syncthreads();
   {
     const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
     for (int i = 0; i < n; ++i) {
@@ -260,9 +271,10 @@ __device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
       sum += __shfl_xor_sync(0xffffffffu, sum, 1);
       sum += __shfl_xor_sync(0xffffffffu, sum, 2);
       if (part == 0 && c <= i) V[i * kPitch + c] = ((c == i ? T(1) : T(0)) - sum) / S[i * kPitch + i];
-      __syncthreads();
+      __syncwarp();
     }
   }
+  __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
     const int i = e % n, j = e / n;
     A[(size_t)i + (size_t)j * lda] = (i >= j) ? S[i * kPitch + j] : T(0);
@@ -284,34 +296,46 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagTask<T>* __restrict
 }
 
 // C[M x N] = beta C + alpha op(A) op(B), M, N <= 64, by the whole CTA, with
-// shared staging As/Bs (kKC x (kTile + 1) each).  Ends with a barrier.
+// shared staging As/Bs (kKC x (kTile + 1) each).  The next K chunk is loaded
+// into registers while the current one is multiplied, so the global load
+// latency overlaps the arithmetic.  Ends with a barrier.
 template <typename T>
 __device__ void cta_gemm(T* C, int ldc, int M, int N, T alpha, int beta, const T* A, int lda, bool ta,
                          const T* B, int ldb, bool tb, int K, T (*As)[kTile + 1], T (*Bs)[kTile + 1]) {
+  constexpr int NL = (kKC * kTile) / kThreads;   // elements of A (and of B) per thread per chunk
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   T acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
-  for (int k0 = 0; k0 < K; k0 += kKC) {
+  T ra[NL], rb[NL];
+  auto load = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < (kKC * kTile) / kThreads; ++q) {
+    for (int q = 0; q < NL; ++q) {
       const int e = threadIdx.x + kThreads * q;
       int i, kk;
       if (!ta) { i = e & 63; kk = e >> 6; } else { kk = e & 15; i = e >> 4; }
-      T v = T(0);
-      if (i < M && k0 + kk < K)
-        v = ta ? A[(size_t)(k0 + kk) + (size_t)i * lda] : A[(size_t)i + (size_t)(k0 + kk) * lda];
-      As[kk][i] = v;
+      ra[q] = (i < M && k0 + kk < K)
+                  ? (ta ? A[(size_t)(k0 + kk) + (size_t)i * lda] : A[(size_t)i + (size_t)(k0 + kk) * lda])
+                  : T(0);
       int j;
       if (!tb) { kk = e & 15; j = e >> 4; } else { j = e & 63; kk = e >> 6; }
-      v = T(0);
-      if (j < N && k0 + kk < K)
-        v = tb ? B[(size_t)j + (size_t)(k0 + kk) * ldb] : B[(size_t)(k0 + kk) + (size_t)j * ldb];
-      Bs[kk][j] = v;
+      rb[q] = (j < N && k0 + kk < K)
+                  ? (tb ? B[(size_t)j + (size_t)(k0 + kk) * ldb] : B[(size_t)(k0 + kk) + (size_t)j * ldb])
+                  : T(0);
+    }
+  };
+  if (K > 0) load(0);
+  for (int k0 = 0; k0 < K; k0 += kKC) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int e = threadIdx.x + kThreads * q;
+      if (!ta) As[e >> 6][e & 63] = ra[q]; else As[e & 15][e >> 4] = ra[q];
+      if (!tb) Bs[e & 15][e >> 4] = rb[q]; else Bs[e >> 6][e & 63] = rb[q];
     }
     __syncthreads();
+    if (k0 + kKC < K) load(k0 + kKC);
 #pragma unroll
     for (int kk = 0; kk < kKC; ++kk) {
       T a[4], b[4];
@@ -342,18 +366,101 @@ __device__ void cta_gemm(T* C, int ldc, int M, int N, T alpha, int beta, const T
   __syncthreads();
 }
 
+// FP32 CTA tile product with the k_gemm<float> scheme: 4x4 blocks of
+// consecutive rows / columns per thread, 16-byte shared-memory operand reads,
+// double-buffered chunks with the next chunk prefetched into registers.
+__device__ void cta_gemm_f(float* C, int ldc, int M, int N, float alpha, int beta, const float* A, int lda,
+                           bool ta, const float* B, int ldb, bool tb, int K, float (*As)[kKC][kPitchF],
+                           float (*Bs)[kKC][kPitchF]) {
+  GemmContrib<float> cb;
+  cb.A = A;
+  cb.B = B;
+  cb.lda = lda;
+  cb.ldb = ldb;
+  cb.K = K;
+  cb.flags = (ta ? kTransA : 0) | (tb ? kTransB : 0);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+  if (K > 0) {
+    float ra[4], rb[4];
+    gemm_load_chunk(cb, M, N, 0, ra, rb);
+    gemm_store_chunk(cb, As[0], Bs[0], ra, rb);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += kKC) {
+      const bool more = k0 + kKC < K;
+      if (more) gemm_load_chunk(cb, M, N, k0 + kKC, ra, rb);
+#pragma unroll
+      for (int kk = 0; kk < kKC; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+      }
+      if (more) {
+        gemm_store_chunk(cb, As[buf ^ 1], Bs[buf ^ 1], ra, rb);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = ty * 4 + r;
+    if (i >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = tx * 4 + q;
+      if (j < N) {
+        float* p = C + (size_t)i + (size_t)j * ldc;
+        float v = alpha * acc[r][q];
+        if (beta) v += *p;
+        *p = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Shared staging of the front kernel's tile products after S and V: the FP32
+// kernel uses the double-buffered 16-byte layout, FP64 the plain one.
+template <typename T>
+struct FrontStage {
+  static size_t bytes() { return 2 * sizeof(T) * kKC * (kTile + 1); }
+  static __device__ void gemm(T* C, int ldc, int M, int N, T alpha, int beta, const T* A, int lda, bool ta,
+                              const T* B, int ldb, bool tb, int K, unsigned char* st) {
+    T (*As)[kTile + 1] = reinterpret_cast<T (*)[kTile + 1]>(st);
+    cta_gemm<T>(C, ldc, M, N, alpha, beta, A, lda, ta, B, ldb, tb, K, As, As + kKC);
+  }
+};
+template <>
+struct FrontStage<float> {
+  static size_t bytes() { return 2 * 2 * sizeof(float) * kKC * kPitchF; }
+  static __device__ void gemm(float* C, int ldc, int M, int N, float alpha, int beta, const float* A, int lda,
+                              bool ta, const float* B, int ldb, bool tb, int K, unsigned char* st) {
+    float (*As)[kKC][kPitchF] = reinterpret_cast<float (*)[kKC][kPitchF]>(st);
+    cta_gemm_f(C, ldc, M, N, alpha, beta, A, lda, ta, B, ldb, tb, K, As, As + 2);
+  }
+};
+
 // Whole blocked Cholesky of an m x m front D with L^{-1} in Li, one CTA per
 // front (small fronts): the same diagonal-tile / panel / trailing-update
 // sweep as the multi-launch path, without a launch per step.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_front(const FrontTask<T>* __restrict__ tasks,
+__global__ void __launch_bounds__(kThreads, 4) k_front(const FrontTask<T>* __restrict__ tasks,
                                                     DevStatus* st, int level) {
   const FrontTask<T> tk = tasks[blockIdx.x];
   extern __shared__ __align__(16) unsigned char smraw[];
   T* S = reinterpret_cast<T*>(smraw);
   T* V = S + kTile * kPitch;
-  T (*As)[kTile + 1] = reinterpret_cast<T (*)[kTile + 1]>(V + kTile * kPitch);
-  T (*Bs)[kTile + 1] = As + kKC;
+  unsigned char* stg = reinterpret_cast<unsigned char*>(V + kTile * kPitch);   // 16-byte aligned
   const int m = tk.m;
   T* D = tk.D;
   T* Li = tk.Li;
@@ -366,22 +473,22 @@ __global__ void __launch_bounds__(kThreads) k_front(const FrontTask<T>* __restri
     if (b && !bad) bad = b;
     for (int ri = r1; ri < m; ri += kTile) {
       T* C = D + ri + (size_t)r0 * m;
-      cta_gemm<T>(C, m, min(kTile, m - ri), nk, T(1), 0, C, m, false, Likk, m, true, nk, As, Bs);
+      FrontStage<T>::gemm(C, m, min(kTile, m - ri), nk, T(1), 0, C, m, false, Likk, m, true, nk, stg);
     }
     for (int j0 = 0; j0 < r0; j0 += kTile) {
       T* C = Li + r0 + (size_t)j0 * m;
-      cta_gemm<T>(C, m, nk, min(kTile, r0 - j0), T(1), 0, Likk, m, false, C, m, false, nk, As, Bs);
+      FrontStage<T>::gemm(C, m, nk, min(kTile, r0 - j0), T(1), 0, Likk, m, false, C, m, false, nk, stg);
     }
     for (int rj = r1; rj < m; rj += kTile) {
       const int nj = min(kTile, m - rj);
       for (int ri = rj; ri < m; ri += kTile)
-        cta_gemm<T>(D + ri + (size_t)rj * m, m, min(kTile, m - ri), nj, T(-1), 1, D + ri + (size_t)r0 * m, m,
-                    false, D + rj + (size_t)r0 * m, m, true, nk, As, Bs);
+        FrontStage<T>::gemm(D + ri + (size_t)rj * m, m, min(kTile, m - ri), nj, T(-1), 1, D + ri + (size_t)r0 * m, m,
+                    false, D + rj + (size_t)r0 * m, m, true, nk, stg);
     }
     for (int ri = r1; ri < m; ri += kTile)
       for (int j0 = 0; j0 < r1; j0 += kTile)
-        cta_gemm<T>(Li + ri + (size_t)j0 * m, m, min(kTile, m - ri), min(kTile, r1 - j0), T(-1), 1,
-                    D + ri + (size_t)r0 * m, m, false, Li + r0 + (size_t)j0 * m, m, false, nk, As, Bs);
+        FrontStage<T>::gemm(Li + ri + (size_t)j0 * m, m, min(kTile, m - ri), min(kTile, r1 - j0), T(-1), 1,
+                    D + ri + (size_t)r0 * m, m, false, Li + r0 + (size_t)j0 * m, m, false, nk, stg);
   }
   if (threadIdx.x == 0 && bad) report(st, bad == 1 ? SGF_ERR_NOT_SPD : SGF_ERR_NONFINITE, level, tk.node);
 }
@@ -1134,7 +1241,7 @@ void launch_front(const FrontTask<T>* tasks, int n, DevStatus* st, int level, cu
     return;
   }
   if (n <= 0) return;
-  const size_t sm = 2 * sizeof(T) * kTile * kPitch + 2 * sizeof(T) * kKC * (kTile + 1);
+  const size_t sm = 2 * sizeof(T) * kTile * kPitch + FrontStage<T>::bytes();
   cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ProfScope ps(P_DIAG, s);
   k_front<T><<<n, kThreads, sm, s>>>(tasks, st, level);

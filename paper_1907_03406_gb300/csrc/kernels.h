@@ -21,9 +21,15 @@ void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* contribs, int n
 template <typename T>
 void launch_diag(const DiagTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
 // whole blocked Cholesky + inverse of small fronts, one CTA each
-constexpr int kFrontSmall = 512;
-// fronts up to kFrontTiny always take the one-CTA kernel; larger ones only in
-// batches of at least kFrontBatchMin (about one per SM)
+// (up to 512 rows in single precision; in double precision the tiled sweep
+// over many CTAs is faster beyond one tile)
+template <typename T>
+constexpr int front_small() {
+  return sizeof(T) == 8 ? 64 : 512;
+}
+// fronts up to kFrontTiny always take the one-CTA kernel (when front_small
+// allows); larger ones only in batches of at least kFrontBatchMin (about one
+// per SM)
 constexpr int kFrontTiny = 128;
 constexpr int kFrontBatchMin = 152;
 template <typename T>
