@@ -51,6 +51,27 @@
 
 namespace sgf {
 
+namespace {
+// Host staging buffers and pinned upload buffers keep their capacity across
+// factorizations on the same thread (page-locking megabytes per
+// factorization costs milliseconds).  A pinned buffer is returned only after
+// the last copy from it has completed.
+std::vector<std::vector<char>>& host_pool() {
+  thread_local std::vector<std::vector<char>> p;
+  return p;
+}
+struct PinnedPool {
+  std::vector<std::pair<char*, size_t>> bufs;
+  ~PinnedPool() {
+    for (auto& b : bufs) cudaFreeHost(b.first);
+  }
+};
+PinnedPool& pinned_pool() {
+  thread_local PinnedPool p;
+  return p;
+}
+}  // namespace
+
 void Batch::run(cudaStream_t s) {
   char* d = nullptr;
   if (!host.empty()) {
@@ -63,6 +84,11 @@ void Batch::run(cudaStream_t s) {
       cur ^= 1;
       if (ev[i]) SGF_CK(cudaEventSynchronize(ev[i]));
       else SGF_CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+      if (!pin[i] && !pinned_pool().bufs.empty()) {   // reuse a pooled buffer
+        pin[i] = pinned_pool().bufs.back().first;
+        pincap[i] = pinned_pool().bufs.back().second;
+        pinned_pool().bufs.pop_back();
+      }
       if (pincap[i] < host.size()) {
         if (pin[i]) cudaFreeHost(pin[i]);
         pincap[i] = std::max(host.size() + host.size() / 2, size_t(1) << 20);
@@ -83,13 +109,29 @@ void Batch::run(cudaStream_t s) {
   launches.clear();
 }
 
+
+Batch::Batch() {
+  auto& p = host_pool();
+  if (!p.empty()) {
+    host.swap(p.back());
+    p.pop_back();
+    host.clear();
+  }
+}
+
 Batch::~Batch() {
+  host.clear();
+  if (host_pool().size() < 8) host_pool().push_back(std::move(host));
   for (int i = 0; i < 2; ++i) {
     if (ev[i]) {
       cudaEventSynchronize(ev[i]);
       cudaEventDestroy(ev[i]);
     }
-    if (pin[i]) cudaFreeHost(pin[i]);
+    if (pin[i]) {
+      auto& q = pinned_pool().bufs;
+      if (q.size() < 8) q.push_back({pin[i], pincap[i]});
+      else cudaFreeHost(pin[i]);
+    }
   }
 }
 
@@ -115,6 +157,38 @@ void Batch::release(cudaStream_t s) {
 
 namespace {
 
+// Vectors handed out with the capacity they reached in earlier use on this
+// thread (task lists are rebuilt for every factorization; growing them from
+// empty each time costs reallocation copies).
+template <class V>
+struct VecPool {
+  static std::vector<V>& pool() {
+    thread_local std::vector<V> p;
+    return p;
+  }
+  static V get() {
+    auto& p = pool();
+    if (p.empty()) return V();
+    V v = std::move(p.back());
+    p.pop_back();
+    v.clear();
+    return v;
+  }
+  static void put(V&& v) {
+    auto& p = pool();
+    if (p.size() < 16) p.push_back(std::move(v));
+  }
+};
+
+template <class V>
+struct Pooled {
+  V v = VecPool<V>::get();
+  Pooled() = default;
+  Pooled(const Pooled&) = delete;
+  Pooled& operator=(const Pooled&) = delete;
+  ~Pooled() { VecPool<V>::put(std::move(v)); }
+};
+
 template <typename T>
 struct Spec {
   const T* A;
@@ -128,8 +202,10 @@ struct Spec {
 
 template <typename T>
 struct GemmList {
-  std::vector<GemmTask<T>> t;
-  std::vector<GemmContrib<T>> c;
+  Pooled<std::vector<GemmTask<T>>> tp;
+  Pooled<std::vector<GemmContrib<T>>> cp;
+  std::vector<GemmTask<T>>& t = tp.v;
+  std::vector<GemmContrib<T>>& c = cp.v;
   void add(T* C, int ldc, int M, int N, T alpha, int beta, std::initializer_list<Spec<T>> specs) {
     add_range(C, ldc, M, N, alpha, beta, specs.begin(), specs.end());
   }
@@ -166,6 +242,16 @@ struct GemmList {
         t.push_back(g);
       }
   }
+  // tasks of another list, after this list's (contribution indices shifted)
+  void append(const GemmList& o) {
+    const int base = (int)c.size();
+    t.reserve(t.size() + o.t.size());
+    for (GemmTask<T> g : o.t) {
+      g.c_begin += base;
+      t.push_back(g);
+    }
+    c.insert(c.end(), o.c.begin(), o.c.end());
+  }
   // C[M x N] = Li B with Li lower triangular (M x M): row tile i0 needs only
   // the first min(M, i0 + 64) rows of B
   void add_lowtri(T* C, int ldc, int M, int N, const T* Li, int ldli, const T* B, int ldb) {
@@ -196,7 +282,8 @@ struct GemmList {
 
 template <typename S, typename D>
 struct CopyList {
-  std::vector<CopyTask<S, D>> t;
+  Pooled<std::vector<CopyTask<S, D>>> tp;
+  std::vector<CopyTask<S, D>>& t = tp.v;
   // dst (rows x cols, ld ldd) <- mode(src); src is rows x cols (cols x rows for kCopyT)
   void add(const S* src, int lds, D* dst, int ldd, int rows, int cols, int mode) {
     for (int j0 = 0; j0 < cols; j0 += kTile)
@@ -216,6 +303,7 @@ struct CopyList {
         t.push_back(k);
       }
   }
+  void append(const CopyList& o) { t.insert(t.end(), o.t.begin(), o.t.end()); }
   void emit(Batch& b, cudaStream_t s) {
     if (t.empty()) return;
     const size_t ot = b.push(t);
@@ -416,6 +504,14 @@ struct GemvList {
     }
   }
 
+  void append(const GemvList& o) {
+    const int base = (int)c.size();
+    for (GemvTask<T> g : o.t) {
+      g.c_begin += base;
+      t.push_back(g);
+    }
+    c.insert(c.end(), o.c.begin(), o.c.end());
+  }
   // Split chunks into tasks of about `budget` elements (and at most kGemvMaxC
   // contributions each); returns the number of partial elements and counters
   // the split chunks need.  Depends on the shapes only, not on nr.
@@ -723,12 +819,16 @@ class FactorImpl final : public FactorBase {
   // SGF_TRACE=1: synchronize and print the wall time of each factor phase
   bool trace_on_ = std::getenv("SGF_TRACE") != nullptr;
   std::chrono::steady_clock::time_point trace_t0_ = std::chrono::steady_clock::now();
+  // (wall time since the previous mark, and the host time spent before this
+  // mark's synchronisation, i.e. building and issuing the phase)
   void trace(cudaStream_t s, int level, const char* what) {
     if (!trace_on_) return;
+    const auto issued = std::chrono::steady_clock::now();
     if (!dry_run()) cudaStreamSynchronize(s);
     const auto now = std::chrono::steady_clock::now();
-    std::fprintf(stderr, "[sgf trace] level %d %-22s %8.3f ms\n", level, what,
-                 std::chrono::duration<double, std::milli>(now - trace_t0_).count());
+    std::fprintf(stderr, "[sgf trace] level %d %-22s %8.3f ms  (host %7.3f ms)\n", level, what,
+                 std::chrono::duration<double, std::milli>(now - trace_t0_).count(),
+                 std::chrono::duration<double, std::milli>(issued - trace_t0_).count());
     trace_t0_ = now;
   }
 
@@ -826,27 +926,60 @@ class FactorImpl final : public FactorBase {
         gw.emit(b, s);
       }
       {
-        // Schur complement, owner-computes per target block
-        std::map<T*, std::pair<std::array<int, 3>, std::vector<Spec<T>>>> tg;
-        for (const auto& r : rec.in) {
+        // Schur complement, owner-computes per target block.  Targets are
+        // numbered (diagonal block of S: S; block (Sa, Sb), Sa < Sb: nn + its
+        // index in Sa's neighbour list); the (target, contribution) pairs are
+        // bucketed by target with a stable counting sort, so each target sums
+        // its contributions in interior order.
+        struct Pair { int id; Spec<T> sp; };
+        const int nin = (int)rec.in.size();
+        const int ntg = nn + (int)lay.up_nb.size();
+        auto tid = [&](int Sa, int Sb) {
+          if (Sa == Sb) return Sa;
+          auto bgn = lay.up_nb.begin() + lay.up_ptr[Sa], end = lay.up_nb.begin() + lay.up_ptr[Sa + 1];
+          auto it = std::lower_bound(bgn, end, Sb);
+          if (it == end || *it != Sb) throw SgfError(SGF_ERR_CUDA, "internal: missing fill block");
+          return nn + (int)(it - lay.up_nb.begin());
+        };
+        Pooled<std::vector<Pair>> pp;
+        std::vector<Pair>& pairs = pp.v;
+        for (int k = 0; k < nin; ++k) {
+          const auto& r = rec.in[k];
           for (size_t a = 0; a < r.nb.size(); ++a)
-            for (size_t c = a; c < r.nb.size(); ++c) {
-              const int Sa = r.nb[a].first, Sb = r.nb[c].first;
-              T* C;
-              if (Sa == Sb) C = Dg + lay.dg_off[Sa];
-              else {
-                const int col = lay.col_of(Sa, Sb);
-                if (col < 0) throw SgfError(SGF_ERR_CUDA, "internal: missing fill block");
-                C = Up + lay.up_off[Sa] + (size_t)col * m[Sa];
-              }
-              auto& e = tg[C];
-              e.first = {m[Sa], m[Sa], m[Sb]};
-              e.second.push_back({r.W + (size_t)r.nb[a].second * r.m, r.m, true,
-                                  r.W + (size_t)r.nb[c].second * r.m, r.m, false, r.m});
-            }
+            for (size_t c = a; c < r.nb.size(); ++c)
+              pairs.push_back({tid(r.nb[a].first, r.nb[c].first),
+                               {r.W + (size_t)r.nb[a].second * r.m, r.m, true,
+                                r.W + (size_t)r.nb[c].second * r.m, r.m, false, r.m}});
+        }
+        std::vector<int> start(ntg + 1, 0);
+        for (const Pair& q : pairs) ++start[q.id + 1];
+        for (int k = 0; k < ntg; ++k) start[k + 1] += start[k];
+        Pooled<std::vector<Spec<T>>> sp;
+        std::vector<Spec<T>>& sorted = sp.v;
+        sorted.resize(start[ntg]);
+        {
+          std::vector<int> fill(start.begin(), start.end() - 1);
+          for (const Pair& q : pairs) sorted[fill[q.id]++] = q.sp;
         }
         GemmList<T> gl;
-        for (auto& kv : tg) gl.add(kv.first, kv.second.first[0], kv.second.first[1], kv.second.first[2], T(-1), 1, kv.second.second);
+        {
+          GemmList<T>& G = gl;
+          for (int k = 0; k < ntg; ++k) {
+            if (start[k] == start[k + 1]) continue;
+            int Sa, Sb;
+            T* C;
+            if (k < nn) {
+              Sa = Sb = k;
+              C = Dg + lay.dg_off[Sa];
+            } else {
+              const int u = k - nn;
+              Sa = (int)(std::upper_bound(lay.up_ptr.begin(), lay.up_ptr.end(), u) - lay.up_ptr.begin()) - 1;
+              Sb = lay.up_nb[u];
+              C = Up + lay.up_off[Sa] + (size_t)lay.up_col[u] * m[Sa];
+            }
+            G.add_range(C, m[Sa], m[Sa], m[Sb], T(-1), 1, sorted.data() + start[k], sorted.data() + start[k + 1]);
+          }
+        }
         gl.emit(b, s);
         b.run(s);
       }
@@ -866,13 +999,20 @@ class FactorImpl final : public FactorBase {
       std::vector<int> sw(ne), cw(ne);
       int64_t t_mm = 0, t_ms = 0, t_mc = 0, t_mp = 0;
       int max_m = 1, max_c = 1;
-      std::vector<std::map<int, int>> gcol(ne);
+      // gofs[B][k]: column offset of neighbour nball[B][k] in B's gathered block
+      std::vector<std::vector<int>> gofs(nn);
       std::vector<int> eidx(nn, -1);
+      auto gcol = [&](int B, int N) {
+        const auto& v = nball[B];
+        const auto it = std::lower_bound(v.begin(), v.end(), N);
+        return gofs[B][it - v.begin()];
+      };
       for (int e = 0; e < ne; ++e) {
         const int B = E[e];
         eidx[B] = e;
         int sB = 0;
-        for (int N : nball[B]) { gcol[e][N] = sB; sB += m[N]; }
+        gofs[B].reserve(nball[B].size());
+        for (int N : nball[B]) { gofs[B].push_back(sB); sB += m[N]; }
         sw[e] = sB;
         cw[e] = pi * (1 + (int)nball[B].size());
         o_mm[e] = t_mm; t_mm += (int64_t)m[B] * m[B];
@@ -897,8 +1037,9 @@ class FactorImpl final : public FactorBase {
         for (int e = 0; e < ne; ++e) {
           const int B = E[e];
           cl.add(Dg + lay.dg_off[B], m[B], Dw + o_mm[e], m[B], m[B], m[B], kCopyLower);
-          for (int N : nball[B]) {
-            T* dst = G + o_ms[e] + (size_t)gcol[e][N] * m[B];
+          for (size_t k = 0; k < nball[B].size(); ++k) {
+            const int N = nball[B][k];
+            T* dst = G + o_ms[e] + (size_t)gofs[B][k] * m[B];
             if (N > B) {
               const int col = lay.col_of(B, N);
               cl.add(Up + lay.up_off[B] + (size_t)col * m[B], m[B], dst, m[B], m[B], m[N], kCopy);
@@ -934,11 +1075,10 @@ class FactorImpl final : public FactorBase {
           const int B = E[e], mb = m[B];
           T* Nb = Nm + o_mc[e];
           gl.add(Nb, mb, mb, pi, T(1), 0, {{Dw + o_mm[e], mb, true, Phi + lay.vec_off[B] * pi, mb, false, mb}});
-          int j = 1;
-          for (int N : nball[B]) {
-            gl.add(Nb + (size_t)j * pi * mb, mb, mb, pi, T(1), 0,
-                   {{Mh + o_ms[e] + (size_t)gcol[e][N] * mb, mb, false, Phi + lay.vec_off[N] * pi, m[N], false, m[N]}});
-            ++j;
+          for (size_t k = 0; k < nball[B].size(); ++k) {
+            const int N = nball[B][k];
+            gl.add(Nb + (size_t)(k + 1) * pi * mb, mb, mb, pi, T(1), 0,
+                   {{Mh + o_ms[e] + (size_t)gofs[B][k] * mb, mb, false, Phi + lay.vec_off[N] * pi, m[N], false, m[N]}});
           }
         }
         gl.emit(b, s);
@@ -986,6 +1126,7 @@ class FactorImpl final : public FactorBase {
         }
         b.run(s);
       }
+      trace(s, lvl, "compression issued");
       check_status(s);
       trace(s, lvl, "compression to QR");
       std::vector<int> rk(ne, 0);
@@ -1065,13 +1206,13 @@ class FactorImpl final : public FactorBase {
           T* K = Kb + ko[q];
           if (comp[C] && !comp[Cp]) {
             g1.add(K, kk[C], kk[C], m[Cp], T(1), 0,
-                   {{Q1 + o_mm[e], m[C], true, Mh + o_ms[e] + (size_t)gcol[e][Cp] * m[C], m[C], false, m[C]}});
+                   {{Q1 + o_mm[e], m[C], true, Mh + o_ms[e] + (size_t)gcol(C, Cp) * m[C], m[C], false, m[C]}});
           } else if (!comp[C] && comp[Cp]) {
             g1.add(K, m[C], m[C], kk[Cp], T(1), 0, {{X, m[C], false, Yh + o_mr[ep], m[Cp], false, m[Cp]}});
           } else {
             T* T1q = T1 + to[q];
             g1.add(T1q, m[C], m[C], kk[Cp], T(1), 0,
-                   {{Mh + o_ms[e] + (size_t)gcol[e][Cp] * m[C], m[C], false, Yh + o_mr[ep], m[Cp], false, m[Cp]}});
+                   {{Mh + o_ms[e] + (size_t)gcol(C, Cp) * m[C], m[C], false, Yh + o_mr[ep], m[Cp], false, m[Cp]}});
             g2.add(K, kk[C], kk[C], kk[Cp], T(1), 0, {{Q1 + o_mm[e], m[C], true, T1q, m[C], false, m[C]}});
           }
           src[q] = {K, kk[C]};

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -40,15 +41,18 @@ struct Batch {
   size_t pincap[2] = {0, 0};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int cur = 0;
-  Batch() = default;
+  Batch();
   Batch(const Batch&) = delete;
   Batch& operator=(const Batch&) = delete;
   ~Batch();
   template <class X>
   size_t push(const std::vector<X>& v) {
-    size_t off = (host.size() + 63) & ~size_t(63);
-    host.resize(off + v.size() * sizeof(X));
-    if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(X));
+    const size_t off = (host.size() + 63) & ~size_t(63);
+    const size_t bytes = v.size() * sizeof(X);
+    if (host.capacity() < off + bytes) host.reserve(std::max(2 * host.capacity(), off + bytes));
+    host.insert(host.end(), off - host.size(), char(0));   // alignment padding only
+    const char* p = reinterpret_cast<const char*>(v.data());
+    host.insert(host.end(), p, p + bytes);
     return off;
   }
   // upload and run everything recorded so far, then reset
