@@ -44,6 +44,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <type_traits>
 
 #include "devmem.h"
 #include "factor.h"
@@ -206,6 +207,9 @@ struct GemmList {
   Pooled<std::vector<GemmContrib<T>>> cp;
   std::vector<GemmTask<T>>& t = tp.v;
   std::vector<GemmContrib<T>>& c = cp.v;
+  // FP32 products go to the tensor cores (3xTF32) in kTileTC-row tiles
+  const bool tc = std::is_same<T, float>::value && gemm_tc_enabled();
+  const int tm = tc ? kTileTC : kTile;
   void add(T* C, int ldc, int M, int N, T alpha, int beta, std::initializer_list<Spec<T>> specs) {
     add_range(C, ldc, M, N, alpha, beta, specs.begin(), specs.end());
   }
@@ -215,11 +219,11 @@ struct GemmList {
   void add_range(T* C, int ldc, int M, int N, T alpha, int beta, const Spec<T>* sb, const Spec<T>* se) {
     if (M <= 0 || N <= 0) return;
     for (int j0 = 0; j0 < N; j0 += kTile)
-      for (int i0 = 0; i0 < M; i0 += kTile) {
+      for (int i0 = 0; i0 < M; i0 += tm) {
         GemmTask<T> g;
         g.C = C + i0 + (size_t)j0 * ldc;
         g.ldc = ldc;
-        g.M = std::min(kTile, M - i0);
+        g.M = std::min(tm, M - i0);
         g.N = std::min(kTile, N - j0);
         g.c_begin = (int)c.size();
         g.alpha = alpha;
@@ -255,9 +259,9 @@ struct GemmList {
   // C[M x N] = Li B with Li lower triangular (M x M): row tile i0 needs only
   // the first min(M, i0 + 64) rows of B
   void add_lowtri(T* C, int ldc, int M, int N, const T* Li, int ldli, const T* B, int ldb) {
-    for (int i0 = 0; i0 < M; i0 += kTile) {
-      const int K = std::min(M, i0 + kTile);
-      add(C + i0, ldc, std::min(kTile, M - i0), N, T(1), 0, {{Li + i0, ldli, false, B, ldb, false, K}});
+    for (int i0 = 0; i0 < M; i0 += tm) {
+      const int K = std::min(M, i0 + tm);
+      add(C + i0, ldc, std::min(tm, M - i0), N, T(1), 0, {{Li + i0, ldli, false, B, ldb, false, K}});
     }
   }
   void emit(Batch& b, cudaStream_t s) {
@@ -271,8 +275,15 @@ struct GemmList {
     for (const auto& g : t) by += (double)sizeof(T) * g.M * g.N * (g.beta ? 2 : 1);
     const size_t ot = b.push(t), oc = b.push(c);
     const int n = (int)t.size();
+    const bool use_tc = tc;
     b.launches.push_back([=](const char* d) {
       prof_work(fl, by);
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_tc) {
+          launch_gemm_tc((const GemmTask<float>*)(d + ot), (const GemmContrib<float>*)(d + oc), n, s);
+          return;
+        }
+      }
       launch_gemm<T>((const GemmTask<T>*)(d + ot), (const GemmContrib<T>*)(d + oc), n, s);
     });
     t.clear();

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 
 #include "devmem.h"
@@ -209,6 +210,306 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core tile GEMM (FP32 in, 3xTF32 products, FP32 accumulation)
+// ---------------------------------------------------------------------------
+// One CTA per kTileTC x kTile output tile; the contributions' K ranges are
+// walked in chunks of kTcKC.  Pipeline per chunk:
+//  1. raw FP32 chunks of op(A) (rows i) and op(B)^T (rows j) are copied into a
+//     ring of kTcStages shared-memory stages by per-thread 4-byte cp.async,
+//     kTcStages - 1 chunks ahead of the arithmetic;
+//  2. once a stage has landed, the threads split it into TF32 high parts
+//     (round to nearest) and FP32 remainders, written K-major in the
+//     no-swizzle canonical layout (core matrices of 8 rows x 16 bytes, along K
+//     128 bytes apart, along rows kTcKC / 4 * 128 bytes apart) into one of two
+//     operand buffers;
+//  3. one thread issues, per 8-wide K step, a_hi b_hi, a_hi b_lo and a_lo b_hi
+//     (tcgen05.mma kind::tf32, M = 128, N = 64) into a 64-column
+//     tensor-memory accumulator and commits them to the buffer's mbarrier, so
+//     the products of chunk i overlap the split of chunk i + 1 and the copies
+//     of the chunks after it.
+// Rows of a buffer beyond the task's M / N hold stale data (they only feed
+// accumulator rows / columns that are never read); K positions beyond a
+// contribution's K are written as zeros.  The epilogue reads the accumulator
+// with tcgen05.ld (warp w: lanes 32 (w mod 4) .. +31, columns 32 (w / 4) ..
+// +31).  Every mbarrier wait is bounded; a wait that gives up poisons the tile
+// with NaN (reported downstream as a non-finite factor) instead of hanging,
+// and the tensor memory is released on every path.
+constexpr int kTcKC = 16;
+constexpr int kTcStages = 4;
+// raw stage: rawA[k][kTcAP] (rows i fastest), rawB[k][kTcBP]; the pitches
+// (multiples of 8 plus 8) make the split's core-matrix reads conflict-free
+constexpr int kTcAP = kTileTC + 8, kTcBP = kTile + 8;
+constexpr int kTcARaw = kTcKC * kTcAP, kTcBRaw = kTcKC * kTcBP;
+constexpr int kTcStage = kTcARaw + kTcBRaw;
+constexpr int kTcAOp = kTileTC * kTcKC, kTcBOp = kTile * kTcKC;   // canonical operand buffers
+constexpr int kTcOp = 2 * (kTcAOp + kTcBOp);                      // hi + lo of A and B
+constexpr size_t kTcSmem = sizeof(float) * ((size_t)kTcStages * kTcStage + 2 * kTcOp);
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  constexpr uint32_t lbo = 128, sbo = (kTcKC / 4) * 128;
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(lbo >> 4) << 16;
+  d |= (uint64_t)(sbo >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version; base offset 0, no swizzle
+  return d;
+}
+// kind::tf32 instruction descriptor: D F32, A and B TF32, both K-major
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) |
+                              ((uint32_t)(kTileTC >> 4) << 24);
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_cp4(uint32_t dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Producer state: the contribution being copied, with this thread's fixed
+// share of each chunk (8 elements of op(A), 4 of op(B)) as base pointers and
+// per-element strides, so a chunk costs one address add per element.
+struct TcProd {
+  int c, k0, K;
+  const float* pa;   // element (row ia, column ka) of op(A) at k0 = 0
+  const float* pb;
+  long long sa, sb;  // pointer step between this thread's elements q and q + 1
+  long long ka_step, kb_step;   // pointer step per unit of k0
+  int ia, ka, ja, kbb;          // this thread's first (row, k) of A and (row, k) of B
+  int dia, dka, djb, dkb;       // (row, k) step per element
+};
+
+__device__ __forceinline__ void tc_prod_set(TcProd& p, const GemmContrib<float>& cb) {
+  const int tid = threadIdx.x;
+  p.K = cb.K;
+  if (!(cb.flags & kTransA)) {   // op(A) = A, M x K column-major: rows contiguous
+    p.ia = tid & (kTileTC - 1); p.ka = tid >> 7; p.dia = 0; p.dka = 2;
+    p.pa = cb.A + p.ia + (size_t)p.ka * cb.lda;
+    p.sa = 2LL * cb.lda;
+    p.ka_step = cb.lda;
+  } else {                       // op(A) = A^T, A is K x M: k contiguous
+    p.ka = tid & (kTcKC - 1); p.ia = tid >> 4; p.dia = 16; p.dka = 0;
+    p.pa = cb.A + p.ka + (size_t)p.ia * cb.lda;
+    p.sa = 16LL * cb.lda;
+    p.ka_step = 1;
+  }
+  if (!(cb.flags & kTransB)) {   // op(B) = B, K x N column-major: k contiguous
+    p.kbb = tid & (kTcKC - 1); p.ja = tid >> 4; p.djb = 16; p.dkb = 0;
+    p.pb = cb.B + p.kbb + (size_t)p.ja * cb.ldb;
+    p.sb = 16LL * cb.ldb;
+    p.kb_step = 1;
+  } else {                       // op(B) = B^T, B is N x K: rows j contiguous
+    p.ja = tid & (kTile - 1); p.kbb = tid >> 6; p.djb = 0; p.dkb = 4;
+    p.pb = cb.B + p.ja + (size_t)p.kbb * cb.ldb;
+    p.sb = 4LL * cb.ldb;
+    p.kb_step = cb.ldb;
+  }
+}
+
+// copies of the producer's current chunk into a raw stage
+__device__ __forceinline__ void tc_issue(const TcProd& p, int M, int N, uint32_t sraw) {
+  const int kc = min(kTcKC, p.K - p.k0);
+  const float* a = p.pa + p.ka_step * p.k0;
+#pragma unroll
+  for (int q = 0; q < kTcAOp / kThreads; ++q) {
+    const int i = p.ia + q * p.dia, k = p.ka + q * p.dka;
+    if (i < M && k < kc) tc_cp4(sraw + 4u * (k * kTcAP + i), a + q * p.sa);
+  }
+  const float* b = p.pb + p.kb_step * p.k0;
+#pragma unroll
+  for (int q = 0; q < kTcBOp / kThreads; ++q) {
+    const int j = p.ja + q * p.djb, k = p.kbb + q * p.dkb;
+    if (j < N && k < kc) tc_cp4(sraw + 4u * (kTcARaw + k * kTcBP + j), b + q * p.sb);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gemm_tc(const GemmTask<float>* __restrict__ tasks,
+                                                      const GemmContrib<float>* __restrict__ cons) {
+  const GemmTask<float> tk = tasks[blockIdx.x];
+  extern __shared__ __align__(1024) unsigned char tc_smraw[];
+  float* ops = reinterpret_cast<float*>(tc_smraw);        // 2 x [Ah | Al | Bh | Bl]
+  float* raw = ops + 2 * kTcOp;                           // kTcStages x [rawA | rawB]
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+  const uint32_t sraw0 = (uint32_t)__cvta_generic_to_shared(raw);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
+                 "r"(kTile)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const int M = tk.M, N = tk.N, cend = tk.c_begin + tk.c_count;
+  // producer (copies) and consumer (split + products) cursors
+  TcProd pr;
+  pr.c = tk.c_begin;
+  while (pr.c < cend && cons[pr.c].K <= 0) ++pr.c;
+  pr.k0 = 0;
+  if (pr.c < cend) tc_prod_set(pr, cons[pr.c]);
+  int cc = pr.c, ck0 = 0, cK = pr.c < cend ? pr.K : 0;
+  auto prod_advance = [&]() {
+    pr.k0 += kTcKC;
+    if (pr.k0 >= pr.K) {
+      pr.k0 = 0;
+      ++pr.c;
+      while (pr.c < cend && cons[pr.c].K <= 0) ++pr.c;
+      if (pr.c < cend) tc_prod_set(pr, cons[pr.c]);
+    }
+  };
+#pragma unroll
+  for (int st = 0; st < kTcStages - 1; ++st) {
+    if (pr.c < cend) {
+      tc_issue(pr, M, N, sraw0 + 4u * st * kTcStage);
+      prod_advance();
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  // split work: core matrices (8 rows x 4 k) holding real rows, one per warp step
+  const int acm = ((M + 7) >> 3) * (kTcKC / 4), bcm = ((N + 7) >> 3) * (kTcKC / 4);
+  const int lr = lane >> 2, lk = lane & 3;
+  int i = 0;
+  uint32_t ph[2] = {0u, 0u};
+  bool bad = false;
+  while (cc < cend) {
+    if (pr.c < cend) {   // its stage held chunk i - 1, split last iteration
+      tc_issue(pr, M, N, sraw0 + 4u * ((i + kTcStages - 1) % kTcStages) * kTcStage);
+      prod_advance();
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 1) : "memory");
+    __syncthreads();   // chunk i landed for every thread
+    const int bsel = i & 1;
+    if (i >= 2) {      // products of chunk i - 2 must be done with this operand buffer
+      if (!tc_wait(mb0 + 8 * bsel, ph[bsel])) { bad = true; break; }
+      ph[bsel] ^= 1;
+    }
+    {
+      const int kc = min(kTcKC, cK - ck0);
+      const float* rA = raw + (i % kTcStages) * kTcStage;
+      const float* rB = rA + kTcARaw;
+      float* Ah = ops + bsel * kTcOp;
+      float* Al = Ah + kTcAOp;
+      float* Bh = Al + kTcAOp;
+      float* Bl = Bh + kTcBOp;
+      for (int cm = warp; cm < acm; cm += kThreads / 32) {
+        const int g = cm / (kTcKC / 4), kq = cm - g * (kTcKC / 4);
+        const int k = 4 * kq + lk, row = 8 * g + lr;
+        const float v = k < kc ? rA[k * kTcAP + row] : 0.f;
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
+        Ah[32 * cm + lane] = __uint_as_float(h);   // core matrix (g, kq): 32 contiguous floats
+        Al[32 * cm + lane] = v - __uint_as_float(h);
+      }
+      for (int cm = warp; cm < bcm; cm += kThreads / 32) {
+        const int g = cm / (kTcKC / 4), kq = cm - g * (kTcKC / 4);
+        const int k = 4 * kq + lk, row = 8 * g + lr;
+        const float v = k < kc ? rB[k * kTcBP + row] : 0.f;
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
+        Bh[32 * cm + lane] = __uint_as_float(h);
+        Bl[32 * cm + lane] = v - __uint_as_float(h);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sAh = (uint32_t)__cvta_generic_to_shared(ops + bsel * kTcOp);
+      const uint32_t sAl = sAh + 4 * kTcAOp, sBh = sAl + 4 * kTcAOp, sBl = sBh + 4 * kTcBOp;
+#pragma unroll
+      for (int st = 0; st < kTcKC / 8; ++st) {
+        const uint32_t ko = st * 2 * 128;   // two core matrices along K per step
+        const uint64_t ah = tc_desc(sAh + ko), al = tc_desc(sAl + ko);
+        const uint64_t bh = tc_desc(sBh + ko), bl = tc_desc(sBl + ko);
+        const uint64_t ad[3] = {ah, ah, al}, bd[3] = {bh, bl, bh};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const uint32_t accum = (i > 0 || st > 0 || t > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad[t]), "l"(bd[t]), "r"(kTcIdesc), "r"(accum)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       mb0 + 8 * bsel)
+                   : "memory");
+    }
+    // consumer cursor
+    ck0 += kTcKC;
+    if (ck0 >= cK) {
+      ck0 = 0;
+      ++cc;
+      while (cc < cend && cons[cc].K <= 0) ++cc;
+      cK = cc < cend ? cons[cc].K : 0;
+    }
+    ++i;
+  }
+  // products still outstanding: the last two chunks' buffers
+  const int n = i;
+  for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) {
+    const int bsel = k & 1;
+    if (!tc_wait(mb0 + 8 * bsel, ph[bsel])) bad = true;
+    ph[bsel] ^= 1;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const int qd = warp & 3, half = warp >> 2;
+  const int row = 32 * qd + lane;
+  uint32_t r[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) r[t] = 0u;
+  if (n > 0 && !bad) {
+    const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * half);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  }
+  if (row < M) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int j = 32 * half + t;
+      if (j < N) {
+        float* p = tk.C + (size_t)row + (size_t)j * tk.ldc;
+        float v = bad ? __int_as_float(0x7fc00000) : tk.alpha * __uint_as_float(r[t]);
+        if (tk.beta) v += *p;
+        *p = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTile) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1208,6 +1509,40 @@ void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* cons, int n, cu
   if (n <= 0) return;
   ProfScope ps(P_GEMM, s);
   k_gemm<T><<<n, kThreads, 0, s>>>(tasks, cons);
+}
+
+bool gemm_tc_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("SGF_TENSOR_CORES");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* cons, int n, cudaStream_t s) {
+  if (dry_run()) {
+    for (int i = 0; i < n; ++i) {
+      const GemmTask<float>& t = tasks[i];
+      if (t.M > kTileTC || t.N > kTile || t.M < 1 || t.N < 1) check_range(nullptr, 1, "tc gemm tile shape");
+      check_block(t.C, t.M, t.N, t.ldc, sizeof(float), "tc gemm C");
+      for (int c = t.c_begin; c < t.c_begin + t.c_count; ++c) {
+        const GemmContrib<float>& q = cons[c];
+        if (q.flags & kTransA) check_block(q.A, q.K, t.M, q.lda, sizeof(float), "tc gemm A^T");
+        else check_block(q.A, t.M, q.K, q.lda, sizeof(float), "tc gemm A");
+        if (q.flags & kTransB) check_block(q.B, t.N, q.K, q.ldb, sizeof(float), "tc gemm B^T");
+        else check_block(q.B, q.K, t.N, q.ldb, sizeof(float), "tc gemm B");
+      }
+    }
+    return;
+  }
+  if (n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    attr = true;
+  }
+  ProfScope ps(P_GEMM, s);
+  k_gemm_tc<<<n, kThreads, kTcSmem, s>>>(tasks, cons);
 }
 
 template <typename T>

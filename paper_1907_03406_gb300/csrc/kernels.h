@@ -18,6 +18,13 @@ struct DevStatus {
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* contribs, int ntasks,
                  cudaStream_t s);
+// FP32 GEMM tasks of up to kTileTC x kTile on the 5th-generation tensor
+// cores: products split into TF32 high and low parts (a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, "3xTF32"), FP32 accumulators in tensor memory
+void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* contribs, int ntasks,
+                    cudaStream_t s);
+// tensor-core GEMMs for the FP32 factor unless SGF_TENSOR_CORES=0
+bool gemm_tc_enabled();
 template <typename T>
 void launch_diag(const DiagTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
 // whole blocked Cholesky + inverse of small fronts, one CTA each

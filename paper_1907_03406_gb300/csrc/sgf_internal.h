@@ -119,11 +119,12 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* o, Plan& plan, std::
 // Device task descriptors (one CTA per task unless stated)
 // ---------------------------------------------------------------------------
 constexpr int kTile = 64;
+constexpr int kTileTC = 128;   // rows of a tensor-core GEMM tile (columns: kTile)
 
 template <typename T>
 struct GemmTask {        // C[M x N] = beta*C + alpha * sum_c op(A_c) op(B_c)
   T* C;
-  int ldc, M, N;         // M, N <= kTile
+  int ldc, M, N;         // M <= kTile (kTileTC on the tensor-core path), N <= kTile
   int c_begin, c_count;  // contribution range
   T alpha;
   int beta;              // 0 or 1

@@ -254,12 +254,19 @@ def test_rigid_body_modes_preserved_on_gpu(name, precision):
     p = np.arange(nx * ny * nz)
     xyz = np.stack([p % nx + 1, (p // nx) % ny, p // (nx * ny)], 1).astype(float)
     R = eval_rbm(xyz, (np.array([nx / 2, ny / 2, nz / 2]), float(max(nx, ny, nz))))
-    tol = 1e-11 if precision == "fp64" else 1e-4   # mixed: tau = 1e-6 truncation + FP32
+    # mixed: tau = 1e-6 truncation, FP32 storage and 3xTF32 tensor-core products
+    # (relative error ~2^-21 per product against FP32's 2^-24, so about 8x the
+    # FP32-only preservation error of ~3e-5)
+    tol = 1e-11 if precision == "fp64" else 1e-3
+    worst = 0.0
     for k in range(6):
         v = _t(R[:, k])
         a = F.apply_forward(v)
         b = F.spmv(v)
-        assert torch.linalg.norm(a - b).item() <= tol * torch.linalg.norm(b).item()
+        err = torch.linalg.norm(a - b).item() / torch.linalg.norm(b).item()
+        worst = max(worst, err)
+        assert err <= tol
+    print(f"{name} {precision}: max relative |A_l r - A r| over the six rigid-body modes {worst:.2e}")
     bvec = _t(si.rhs(plan.n, 0))
     x, info = F.pcg(bvec, rtol=1e-10, maxit=1000)
     assert info["rel_residual"] <= 1e-10
