@@ -219,8 +219,10 @@ const char* sgf_dry_run_report(void);
 /* Launch accounting for benchmarks.  Kernel kinds 0..10 are named by
  * sgf_profile_kind_name (k_gemm, k_diag, k_copy, k_qrcp, k_gemv_n, k_gemv_t,
  * k_veccopy, k_assemble, k_spmv, k_dot, k_vector).  sgf_profile_reset clears
- * the counters; with timing != 0 every later launch is bracketed by CUDA
- * events on its own stream.  sgf_profile_read (synchronizes on the recorded
+ * the counters; with timing = 1 every later launch is bracketed by CUDA
+ * events on its own stream, with timing = 2 only the factor's contraction
+ * launches (k_gemm, k_diag, k_qrcp: far fewer, so the events barely perturb a
+ * timed step), with 0 none.  sgf_profile_read (synchronizes on the recorded
  * events) returns, for one kind, the launches since the reset, their summed
  * device time in ms (0 without timing) and the algorithmic flops and bytes
  * the host attached to them.  Not thread-safe with concurrent factors.      */

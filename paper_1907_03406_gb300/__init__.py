@@ -209,9 +209,12 @@ def solve_host(plan: Plan, coeffs: np.ndarray, b: np.ndarray, rtol=1e-10, maxit=
     return x, dict(iterations=info.iterations, rel_residual=info.rel_residual, seconds=info.seconds)
 
 
-def profile_reset(timing: bool = False):
-    """Clear the launch counters; with timing, bracket every launch with CUDA events."""
-    L.load().sgf_profile_reset(1 if timing else 0)
+def profile_reset(timing=False):
+    """Clear the launch counters.  timing: False (none), True or "all" (every
+    launch bracketed by CUDA events), "contractions" (only the factor's GEMM,
+    front and QR launches)."""
+    mode = {False: 0, True: 1, "all": 1, "contractions": 2}[timing]
+    L.load().sgf_profile_reset(mode)
 
 
 def profile_read() -> dict:

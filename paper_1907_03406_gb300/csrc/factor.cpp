@@ -324,6 +324,20 @@ struct CopyList {
   }
 };
 
+// Upper triangle of a lower-triangular m x m block (ld m) <- the transpose of
+// its lower triangle, so that row i of the lower factor is also available
+// contiguously as column i (the apply reads both L^{-1} x and L^{-T} x as
+// column dot products).  Only once the factor no longer needs the zeros.
+template <typename T>
+void add_mirror(CopyList<T, T>& cl, T* Li, int m) {
+  for (int j0 = 0; j0 < m; j0 += kTile)
+    for (int i0 = 0; i0 <= j0; i0 += kTile) {
+      const int ni = std::min(kTile, m - i0), nj = std::min(kTile, m - j0);
+      if (i0 == j0) cl.add(Li + i0 + (size_t)i0 * m, m, Li + i0 + (size_t)i0 * m, m, ni, ni, kMirror);
+      else cl.add(Li + j0 + (size_t)i0 * m, m, Li + i0 + (size_t)j0 * m, m, ni, nj, kCopyT);
+    }
+}
+
 template <typename T>
 struct Front {
   T* D;   // m x m, ld m (lower part used)
@@ -427,6 +441,7 @@ template <typename T>
 struct InteriorRec {
   int node, m, s;
   T *L, *Li, *W;
+  T* Wt;   // W^T (s x m), for the apply's backward W x_S as column dot products
   std::vector<std::pair<int, int>> nb;  // (separator, column offset in W)
 };
 
@@ -479,6 +494,7 @@ struct GemvList {
     int K;
     bool tri;
     T alpha;
+    bool upper = false;   // tri: the upper triangle (op T: rows <= column)
   };
   // y[M] = beta y + sum alpha op(A)(x - x2); op N chunks of kGemvBand rows,
   // op T chunks of kGemvCols columns (one unsplit task each until emit)
@@ -502,9 +518,10 @@ struct GemvList {
         q.lda = in.lda;
         q.K = in.K;
         q.tri = in.tri ? i0 + 1 : 0;
+        q.upper = in.upper ? 1 : 0;
         q.alpha = in.alpha;
         int kb, ke;
-        gemv_useful(trans, q.tri, q.K, g.M, &kb, &ke);
+        gemv_useful(trans, q.tri, q.upper, q.K, g.M, &kb, &ke);
         total += ke - kb;
         c.push_back(q);
         ++cnt;
@@ -535,7 +552,7 @@ struct GemvList {
       for (int k = 0; k < g.c_count; ++k) {
         const GemvContrib<T>& q = c[g.c_begin + k];
         int kb, ke;
-        gemv_useful(trans, q.tri, q.K, g.M, &kb, &ke);
+        gemv_useful(trans, q.tri, q.upper, q.K, g.M, &kb, &ke);
         pre.push_back(pre.back() + ke - kb);
       }
       const int total = pre.back();
@@ -595,8 +612,8 @@ struct GemvList {
         double el = (double)g.M * c[k].K;
         if (c[k].tri) {
           const double lo = c[k].tri - 1, hi = lo + g.M;  // absolute rows / columns of the chunk
-          el = trans ? (double)g.M * c[k].K - 0.5 * (hi * (hi - 1) - lo * (lo - 1))
-                     : 0.5 * ((hi) * (hi + 1) - lo * (lo + 1));
+          el = (trans && !c[k].upper) ? (double)g.M * c[k].K - 0.5 * (hi * (hi - 1) - lo * (lo - 1))
+                                      : 0.5 * ((hi) * (hi + 1) - lo * (lo + 1));
         }
         fl += 2.0 * el;
         el_all += el;
@@ -892,6 +909,12 @@ class FactorImpl final : public FactorBase {
         if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl);
         b.run(s);
         check_status(s);
+        if (mtop_ > 0) {
+          CopyList<T, T> cm;
+          add_mirror(cm, Litop_, mtop_);
+          cm.emit(b, s);
+          b.run(s);
+        }
         ls.size_before = ls.size_after = mtop_;
         ls.bytes = (int64_t)2 * mtop_ * mtop_ * sizeof(T);
         stats.push_back(ls);
@@ -923,6 +946,7 @@ class FactorImpl final : public FactorBase {
         r.L = Dg + lay.dg_off[i];
         r.Li = LiI + li_off[i];
         r.W = Wb + w_off[i];
+        r.Wt = nullptr;
         for (int k = lay.up_ptr[i]; k < lay.up_ptr[i + 1]; ++k) r.nb.push_back({lay.up_nb[k], lay.up_col[k]});
         rec.in.push_back(r);
       }
@@ -1289,8 +1313,27 @@ class FactorImpl final : public FactorBase {
         }
         rec.sep.push_back(sr);
       }
+      // apply layout: mirrored inverse factors and W^T (the factor is done with
+      // the zero upper triangles of L^{-1} at this point)
+      {
+        int64_t wt_tot = 0;
+        for (const auto& r : rec.in) wt_tot += (int64_t)r.m * r.s;
+        T* Wt = dalloc<T>(keep_, wt_tot, s, false);
+        CopyList<T, T> cm;
+        int64_t off = 0;
+        for (auto& r : rec.in) {
+          add_mirror(cm, r.Li, r.m);
+          r.Wt = Wt + off;
+          off += (int64_t)r.m * r.s;
+          if (r.s > 0) cm.add(r.W, r.m, r.Wt, r.s, r.s, r.m, kCopyT);
+        }
+        for (const auto& sr : rec.sep)
+          if (sr.comp) add_mirror(cm, sr.Li, sr.m);
+        cm.emit(b, s);
+        b.run(s);
+      }
       int64_t bytes = 0;
-      for (const auto& r : rec.in) bytes += ((int64_t)2 * r.m * r.m + (int64_t)r.m * r.s) * sizeof(T);
+      for (const auto& r : rec.in) bytes += ((int64_t)2 * r.m * r.m + (int64_t)2 * r.m * r.s) * sizeof(T);
       for (const auto& r : rec.sep)
         if (r.comp) bytes += ((int64_t)2 * r.m * r.m + (int64_t)r.m * r.k) * sizeof(T);
       ls.bytes = bytes;
@@ -1369,10 +1412,13 @@ class FactorImpl final : public FactorBase {
       T* v = base(t);
       T* w = v + vs * nr;
       T* kp = v + 2 * vs * nr;
+      // every large product is a column dot product: L^{-1} x through the
+      // mirrored upper triangle, W^T x and L^{-T} x through the columns
       GemvList<T> f1(nr), f2(nr), f3(nr), f4(nr);
-      f2.trans = f4.trans = true;
+      f1.trans = f2.trans = f3.trans = f4.trans = true;
       for (const auto& r : R.in)
-        f1.add(w + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+        f1.add(w + nr * lay.vec_off[r.node], r.m, 0,
+               {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1), true}});
       auto si = sep_interiors(R, (int)lay.m.size());
       for (int S = 0; S < (int)si.size(); ++S) {
         if (si[S].empty()) continue;
@@ -1385,7 +1431,8 @@ class FactorImpl final : public FactorBase {
       }
       for (const auto& c : R.sep) {
         if (!c.comp) continue;
-        f3.add(w + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+        f3.add(w + nr * lay.vec_off[c.node], c.m, 0,
+               {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1), true}});
         f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
       }
       f1.emit(P, s);
@@ -1402,8 +1449,8 @@ class FactorImpl final : public FactorBase {
       T* v = vtop_;
       T* w = vtop_ + (size_t)mtop_ * nr;
       GemvList<T> a(nr), bt(nr);
-      bt.trans = true;
-      a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1)}});
+      a.trans = bt.trans = true;
+      a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1), true}});
       bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
       a.emit(P, s);
       bt.emit(P, s);
@@ -1421,21 +1468,45 @@ class FactorImpl final : public FactorBase {
         if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
       veccopy(P, vc, vn, v);
       GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
-      b2.trans = b4.trans = true;
+      b2.trans = b3.trans = b4.trans = true;
       for (const auto& c : R.sep) {
         if (!c.comp) continue;
         b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
         b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
       }
-      for (const auto& r : R.in) {
-        std::vector<typename GemvList<T>::In> ins;
+      // w_I -= W x_S: the separator values of every interior are gathered into
+      // one contiguous vector in W's column order, so each row of W (a column
+      // of W^T) is a single dense dot product
+      std::vector<int> gidx;
+      std::vector<int64_t> goff(R.in.size());
+      for (size_t a = 0; a < R.in.size(); ++a) {
+        const auto& r = R.in[a];
+        goff[a] = (int64_t)gidx.size();
+        gidx.resize(gidx.size() + r.s);
         for (auto [S, col] : r.nb)
-          ins.push_back({r.W + (size_t)col * r.m, r.m, v + nr * lay.vec_off[S], nullptr, lay.m[S], false, T(-1)});
-        b3.add(w + nr * lay.vec_off[r.node], r.m, 1, ins);
+          for (int j = 0; j < lay.m[S]; ++j) gidx[goff[a] + col + j] = (int)(lay.vec_off[S] + j);
+      }
+      T* xs = nullptr;
+      if (!gidx.empty()) {
+        xs = (T*)dev_malloc(sizeof(T) * gidx.size() * nr);
+        P.mem.push_back(xs);
+      }
+      for (size_t a = 0; a < R.in.size(); ++a) {
+        const auto& r = R.in[a];
+        if (r.s > 0) b3.add(w + nr * lay.vec_off[r.node], r.m, 1, {{r.Wt, r.s, xs + nr * goff[a], nullptr, r.s, false, T(-1)}});
         b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
       }
       b1.emit(P, s);
       b2.emit(P, s);
+      if (!gidx.empty()) {
+        const size_t oi = P.b.push(gidx);
+        const int ng = (int)gidx.size(), r = nr;
+        const T* src = v;
+        P.acct.push_back({P_VECCOPY, 0.0, 2.0 * sizeof(T) * ng * r + 4.0 * ng});
+        P.ops.push_back([=](const char* d, cudaStream_t st) {
+          launch_vgather<T>(src, (const int*)(d + oi), xs, ng, r, st);
+        });
+      }
       b3.emit(P, s);
       b4.emit(P, s);
     }

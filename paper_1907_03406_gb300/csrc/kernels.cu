@@ -803,6 +803,10 @@ __global__ void __launch_bounds__(kThreads) k_copy(const CopyTask<S, D>* __restr
   const int n = tk.rows * tk.cols;
   for (int e = threadIdx.x; e < n; e += kThreads) {
     const int i = e % tk.rows, j = e / tk.rows;
+    if (tk.mode == kMirror) {   // upper entries of the tile from their transposes
+      if (i < j) tk.dst[(size_t)i + (size_t)j * tk.ldd] = (D)tk.src[(size_t)j + (size_t)i * tk.lds];
+      continue;
+    }
     D v;
     switch (tk.mode) {
       case kCopy: v = (D)tk.src[(size_t)i + (size_t)j * tk.lds]; break;
@@ -1001,7 +1005,7 @@ __device__ __forceinline__ void gemv_stage(const GemvTask<T>& tk, const GemvCont
     if (t < tk.c_count) {
       const GemvContrib<T> c = cons[tk.c_begin + t];
       int kb, ke;
-      gemv_useful(trans, c.tri, c.K, tk.M, &kb, &ke);
+      gemv_useful(trans, c.tri, c.upper, c.K, tk.M, &kb, &ke);
       S.c[t] = c;
       S.kb[t] = kb;
       len = ke - kb;
@@ -1186,8 +1190,9 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restri
     if (f0 >= f1) continue;
     const GemvContrib<T>& cb = S.c[c];
     int i0 = S.kb[c] + (f0 - S.pre[c]);
-    const int i1 = S.kb[c] + (f1 - S.pre[c]);
-    if (cb.tri) i0 = max(i0, cb.tri - 1 + o);
+    int i1 = S.kb[c] + (f1 - S.pre[c]);
+    if (cb.tri && !cb.upper) i0 = max(i0, cb.tri - 1 + o);
+    if (cb.tri && cb.upper) i1 = min(i1, cb.tri + o);   // rows <= tri - 1 + o
     if (i1 > i0) l2_prefetch(cb.A + (size_t)o * cb.lda + i0, sizeof(T) * (size_t)(i1 - i0));
   }
   T acc[CW][NR];
@@ -1217,8 +1222,10 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restri
 #pragma unroll
         for (int u = 0; u < CW; ++u) {
           const int o = w + kWarps * u;
-          // lower-triangular: rows above the column's absolute index are zero
-          av[u] = (o < tk.M && (!cb.tri || i >= cmin + kWarps * u)) ? a[u * cstep + i] : T(0);
+          // triangular: rows above (lower) or below (upper) the column's
+          // absolute index are zero
+          const bool in_tri = !cb.tri || (cb.upper ? i <= cmin + kWarps * u : i >= cmin + kWarps * u);
+          av[u] = (o < tk.M && in_tri) ? a[u * cstep + i] : T(0);
         }
 #pragma unroll
         for (int u = 0; u < CW; ++u)
@@ -1237,6 +1244,17 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restri
     }
   }
   gemv_finish(tk, tk.M * NR);
+}
+
+// dst[p * nr + q] = src[idx[p] * nr + q]: gathers scattered level-vector
+// entries into one contiguous vector (nr interleaved right-hand sides)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_vgather(const T* __restrict__ src, const int* __restrict__ idx,
+                                                      T* __restrict__ dst, int n, int nr) {
+  const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (e >= (int64_t)n * nr) return;
+  const int64_t p = e / nr, q = e - p * nr;
+  dst[e] = src[(int64_t)idx[p] * nr + q];
 }
 
 template <typename T>
@@ -1591,6 +1609,10 @@ void launch_copy(const CopyTask<S, D>* tasks, int n, cudaStream_t s) {
       check_block(t.dst, t.rows, t.cols, t.ldd, sizeof(D), "copy dst");
       if (t.mode == kCopy || t.mode == kCopyLower) check_block(t.src, t.rows, t.cols, t.lds, sizeof(S), "copy src");
       if (t.mode == kCopyT) check_block(t.src, t.cols, t.rows, t.lds, sizeof(S), "copyT src");
+      if (t.mode == kMirror) {
+        if (t.rows != t.cols) check_range(nullptr, 1, "mirror tile shape");
+        check_block(t.src, t.rows, t.cols, t.lds, sizeof(S), "mirror src");
+      }
     }
     return;
   }
@@ -1639,8 +1661,9 @@ static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int
       else check_block(q.A, t.M, q.K, q.lda, sizeof(T), "gemv A");
       check_range(q.x, sizeof(T) * q.K * nr, "gemv x");
       if (q.x2) check_range(q.x2, sizeof(T) * q.K * nr, "gemv x2");
+      if (q.upper && (!trans || !q.tri)) check_range(nullptr, 1, "gemv upper triangle needs op T");
       int kb, ke;
-      gemv_useful(trans, q.tri, q.K, t.M, &kb, &ke);
+      gemv_useful(trans, q.tri, q.upper, q.K, t.M, &kb, &ke);
       total += ke - kb;
     }
     if (t.k_lo < 0 || t.k_hi > total || (t.k_lo >= t.k_hi && total > 0))
@@ -1686,6 +1709,20 @@ void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, 
     case 4: k_gemv_t<T, 4><<<n, kThreads, 0, s>>>(tasks, cons); break;
     default: k_gemv_t<T, 8><<<n, kThreads, 0, s>>>(tasks, cons); break;
   }
+}
+
+template <typename T>
+void launch_vgather(const T* src, const int* idx, T* dst, int n, int nr, cudaStream_t s) {
+  if (dry_run()) {
+    // (idx is task data in the batch, read here on the host like task lists)
+    check_range(dst, sizeof(T) * (size_t)n * nr, "vgather dst");
+    for (int p = 0; p < n; ++p) check_range(src + (size_t)idx[p] * nr, sizeof(T) * nr, "vgather src");
+    return;
+  }
+  if (n <= 0) return;
+  ProfScope ps(P_VECCOPY, s);
+  const int64_t tot = (int64_t)n * nr;
+  k_vgather<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(src, idx, dst, n, nr);
 }
 
 template <typename T>
@@ -1825,6 +1862,7 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
   template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int,           \
                                  cudaStream_t);                                                  \
   template void launch_veccopy<T>(const VecCopyTask*, int, const T*, T*, cudaStream_t);         \
+  template void launch_vgather<T>(const T*, const int*, T*, int, int, cudaStream_t);           \
   template void launch_assemble_scalar<T>(const double*, int, int, int, unsigned, double,       \
                                           const int64_t*, int64_t, T*, T*, double*, double*,    \
                                           double*, double*, cudaStream_t);                       \

@@ -57,6 +57,9 @@ void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int
 template <typename T>
 void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr,
                    cudaStream_t s);
+// dst[p * nr + q] = src[idx[p] * nr + q], p < n
+template <typename T>
+void launch_vgather(const T* src, const int* idx, T* dst, int n, int nr, cudaStream_t s);
 template <typename T>
 void launch_veccopy(const VecCopyTask* tasks, int ntasks, const T* src, T* dst, cudaStream_t s);
 

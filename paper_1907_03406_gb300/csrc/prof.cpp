@@ -69,7 +69,8 @@ ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
   a.flops += S.next_flops;
   a.bytes += S.next_bytes;
   S.next_flops = S.next_bytes = 0;
-  if (S.timing) {
+  const bool timed = S.timing == 1 || (S.timing == 2 && (kind == P_GEMM || kind == P_DIAG || kind == P_QR));
+  if (timed) {
     Pending p;
     p.a = get_event(S);
     p.b = get_event(S);

@@ -32,6 +32,7 @@ void prof_count(int kind, double flops, double bytes);
 // while a stream capture records launches, they are neither counted nor timed
 void prof_capture(bool on);
 
+// timing: 0 none, 1 every launch, 2 the factor contractions (GEMM, fronts, QR)
 void prof_reset(int timing);
 int prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes);
 const char* prof_name(int kind);

@@ -139,7 +139,9 @@ struct GemmContrib {
   int lda, ldb, K, flags;
 };
 
-enum : int { kCopy = 0, kCopyT = 1, kZero = 2, kIdentity = 3, kCopyLower = 4 };
+// kMirror: in place on a square diagonal tile, upper part <- transpose of
+// the lower part (src == dst)
+enum : int { kCopy = 0, kCopyT = 1, kZero = 2, kIdentity = 3, kCopyLower = 4, kMirror = 5 };
 
 template <typename S, typename D>
 struct CopyTask {        // dst[rows x cols] <- mode(src), rows, cols <= kTile
@@ -198,20 +200,23 @@ struct GemvContrib {
   const T* x;            // K
   const T* x2;           // K or nullptr (subtracted from x)
   int lda, K;
-  int tri;               // 0: dense A; t > 0: A is (part of) a lower-triangular
-                         // matrix whose first row (op N) / column (op T) in this
-                         // chunk has absolute index t - 1: the zero half is skipped
+  int tri;               // 0: dense A; t > 0: A is (part of) a triangular matrix
+                         // whose first row (op N) / column (op T) in this chunk
+                         // has absolute index t - 1: the zero half is skipped
+  int upper;             // tri, op T only: upper triangle (rows <= column) instead
+                         // of lower (rows >= column)
   T alpha;
 };
 
 // Useful index range [kb, ke) of a contribution to a chunk of M outputs: all K
 // for a dense block; for a lower-triangular one the columns j <= last row (op
-// N) or the rows i >= first column (op T).
-SGF_HD inline void gemv_useful(bool trans, int tri, int K, int M, int* kb, int* ke) {
+// N) or the rows i >= first column (op T); for an upper-triangular one (op T)
+// the rows i <= last column.
+SGF_HD inline void gemv_useful(bool trans, int tri, int upper, int K, int M, int* kb, int* ke) {
   if (!tri) {
     *kb = 0;
     *ke = K;
-  } else if (trans) {
+  } else if (trans && !upper) {
     *kb = tri - 1 < K ? tri - 1 : K;
     *ke = K;
   } else {
