@@ -66,6 +66,24 @@ void dev_free(void* p) {
 }
 void* dev_malloc_async(size_t bytes, cudaStream_t s) {
   if (dry_run()) return fake_alloc(bytes);
+  {
+    // keep freed stream-ordered memory cached in this process (the default
+    // release threshold of 0 hands it back at every synchronisation, and each
+    // factorization would reserve its work buffers again)
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (dev >= 0 && dev < 64 && !done[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      done[dev] = true;
+    }
+  }
   void* p = nullptr;
   SGF_CK(cudaMallocAsync(&p, bytes, s));
   return p;

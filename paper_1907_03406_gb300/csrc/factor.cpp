@@ -79,10 +79,10 @@ void Batch::run(cudaStream_t s) {
     if (dry_run()) {
       d = host.data();
     } else {
-      // pinned staging, two buffers in turn: a buffer is refilled only after
-      // the copy that last read it has completed
+      // pinned staging ring: a buffer is refilled only after the copy that
+      // last read it has completed
       const int i = cur;
-      cur ^= 1;
+      cur = (cur + 1) % kRing;
       if (ev[i]) SGF_CK(cudaEventSynchronize(ev[i]));
       else SGF_CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
       if (!pin[i] && !pinned_pool().bufs.empty()) {   // reuse a pooled buffer
@@ -123,14 +123,14 @@ Batch::Batch() {
 Batch::~Batch() {
   host.clear();
   if (host_pool().size() < 8) host_pool().push_back(std::move(host));
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kRing; ++i) {
     if (ev[i]) {
       cudaEventSynchronize(ev[i]);
       cudaEventDestroy(ev[i]);
     }
     if (pin[i]) {
       auto& q = pinned_pool().bufs;
-      if (q.size() < 8) q.push_back({pin[i], pincap[i]});
+      if (q.size() < 2 * kRing) q.push_back({pin[i], pincap[i]});
       else cudaFreeHost(pin[i]);
     }
   }
@@ -680,9 +680,7 @@ class FactorImpl final : public FactorBase {
     dev_memset(st_, 0, sizeof(DevStatus), s);
     try {
       build(coeffs, s);
-      trace(s, 0, "factor levels done");
-      build_programs(s);
-      trace(s, 0, "apply programs");
+      trace(s, 0, "apply programs + top");
     } catch (...) {
       release();
       throw;
@@ -908,13 +906,17 @@ class FactorImpl final : public FactorBase {
         std::vector<Front<T>> F = {{Dg, mtop_, nullptr, 0, Litop_, 0}};
         if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl);
         b.run(s);
-        check_status(s);
-        if (mtop_ > 0) {
+        if (mtop_ > 0) {   // stream ordered after the top factor
           CopyList<T, T> cm;
           add_mirror(cm, Litop_, mtop_);
           cm.emit(b, s);
           b.run(s);
         }
+        trace(s, lvl, "top factor issued");
+        // the apply program is built on the host while the GPU finishes the
+        // top factor; a failed pivot below discards it with the factor
+        build_programs(s);
+        check_status(s);
         ls.size_before = ls.size_after = mtop_;
         ls.bytes = (int64_t)2 * mtop_ * mtop_ * sizeof(T);
         stats.push_back(ls);

@@ -37,9 +37,12 @@ struct Batch {
   std::vector<std::function<void(const char*)>> launches;
   char* dev = nullptr;   // persistent programs only
   size_t cap = 0;
-  char* pin[2] = {nullptr, nullptr};
-  size_t pincap[2] = {0, 0};
-  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // pinned staging ring: a buffer is refilled only after the copy that last
+  // read it has completed, so a deep ring keeps the host from waiting on the GPU
+  static constexpr int kRing = 8;
+  char* pin[kRing] = {};
+  size_t pincap[kRing] = {};
+  cudaEvent_t ev[kRing] = {};
   int cur = 0;
   Batch();
   Batch(const Batch&) = delete;
