@@ -1175,7 +1175,8 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restri
 // segments are prefetched into L2 first; lanes then stride over the flat rows
 // of each contribution, and the lane sums are combined by a butterfly.
 template <typename T, int NR>
-__global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restrict__ tasks,
+__global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
+    k_gemv_t(const GemvTask<T>* __restrict__ tasks,
                                                      const GemvContrib<T>* __restrict__ cons) {
   constexpr int kWarps = kThreads / 32;
   constexpr int CW = kGemvCols / kWarps;
@@ -1209,7 +1210,8 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t(const GemvTask<T>* __restri
       const T* a = cb.A + (size_t)w * cb.lda;
       const size_t cstep = (size_t)kWarps * cb.lda;
       const int cmin = cb.tri ? cb.tri - 1 + w : 0;   // absolute column of u = 0
-#pragma unroll 2
+      constexpr int kUnroll = (sizeof(T) == 4 && NR <= 2) ? 4 : 2;   // row steps in flight
+#pragma unroll kUnroll
       for (int i = i0 + lane; i < i1; i += 32) {
         T xv[NR];
 #pragma unroll
