@@ -126,6 +126,41 @@ int sgf_plan_export_level(const sgf_plan* plan, int level, int* nnodes, int* npa
  * node sizes), for FP64 and for mixed precision; used for admission.        */
 int sgf_plan_footprint(const sgf_plan* plan, size_t* bytes_fp64, size_t* bytes_mixed);
 
+/* ---- launch-shape tuning ---------------------------------------------------
+ * Parameters of the batched launches that change speed and the order of
+ * floating-point sums, not the method (Sec. 4 is unchanged by them).  Kept per
+ * plan; every later sgf_factor of the plan uses them.
+ *   gemv_min_elems, gemv_max_elems: element budget of one apply GEMV task
+ *     (a launch's elements spread over about eight tasks per SM, clamped to
+ *     this range); 256 <= min <= max <= 1 << 20.
+ *   front_small: largest front (rows) the one-CTA elimination kernel takes in
+ *     a batch of at least one front per SM (single precision); 64..512.
+ *   tensor_cores: 1 = single-precision factor GEMMs on the tensor cores as
+ *     3xTF32 split products, 0 = FP32 CUDA cores.
+ * Defaults: 4096, 32768, 512, 1.                                             */
+typedef struct {
+  int gemv_min_elems;
+  int gemv_max_elems;
+  int front_small;
+  int tensor_cores;
+} sgf_tuning;
+
+/* Current tuning of a plan (INVALID_ARG on NULL). */
+int sgf_plan_get_tuning(const sgf_plan* plan, sgf_tuning* out);
+/* Replace the tuning of a plan; INVALID_ARG (plan unchanged) when a field is
+ * outside the ranges above.  Factors made before keep their launch shapes.  */
+int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t);
+/* Autotuner: for each candidate of a small grid of tunings (GEMV budgets x,
+ * in single precision, front_small x tensor_cores; the defaults included),
+ * times with CUDA events on `stream` one sgf_factor of coeffs_dev plus
+ * napply applications of A_l^{-1} (napply >= 0) to a fixed vector, after one
+ * untimed warm-up factorization, and keeps the fastest in the plan.  Writes
+ * it to *best and its time (ms) to *best_ms when not NULL.  Allocates and
+ * frees device memory; synchronizes the stream.  Errors: those of
+ * sgf_factor; on error the plan keeps its previous tuning.                  */
+int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int napply, sgf_tuning* best,
+                 double* best_ms);
+
 /* ---- numeric factorization ----------------------------------------------
  * sgf_factor: Algorithm 4.1 on the device.  coeffs_dev holds one FP64
  * coefficient per cell (natural order).  Per level: batched elimination of

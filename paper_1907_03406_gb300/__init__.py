@@ -118,6 +118,27 @@ class Plan:
         _check(self._lib.sgf_plan_footprint(self.handle, C.byref(a), C.byref(b)), "sgf_plan_footprint")
         return a.value, b.value
 
+    @property
+    def tuning(self) -> dict:
+        """Launch shapes later factors of this plan use (sgf_plan_get_tuning)."""
+        t = L.sgf_tuning()
+        _check(self._lib.sgf_plan_get_tuning(self.handle, C.byref(t)), "sgf_plan_get_tuning")
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    @tuning.setter
+    def tuning(self, values: dict):
+        t = L.sgf_tuning(**{**self.tuning, **values})
+        _check(self._lib.sgf_plan_set_tuning(self.handle, C.byref(t)), "sgf_plan_set_tuning")
+
+    def autotune(self, coeffs, napply: int = 10, stream=None):
+        """Grid search of the launch shapes on one factorization + napply
+        applies (sgf_autotune); keeps the fastest in the plan and returns
+        (tuning dict, ms)."""
+        t, ms = L.sgf_tuning(), C.c_double()
+        _check(self._lib.sgf_autotune(self.handle, _dev_ptr(coeffs), _stream_ptr(stream), int(napply),
+                                      C.byref(t), C.byref(ms)), "sgf_autotune")
+        return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

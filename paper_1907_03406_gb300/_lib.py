@@ -16,6 +16,11 @@ class sgf_grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("dof", C.c_int), ("dirichlet", C.c_uint)]
 
 
+class sgf_tuning(C.Structure):
+    _fields_ = [("gemv_min_elems", C.c_int), ("gemv_max_elems", C.c_int), ("front_small", C.c_int),
+                ("tensor_cores", C.c_int)]
+
+
 class sgf_opts(C.Structure):
     _fields_ = [("scheme", C.c_int), ("leaf", C.c_int), ("degree", C.c_int), ("basis", C.c_int),
                 ("precision", C.c_int), ("tau", C.c_double), ("compress_from_level", C.c_int),
@@ -39,6 +44,9 @@ SIGNATURES = {
     "sgf_plan_info": (_I, [_P, _IP, _I64P]),
     "sgf_plan_export_level": (_I, [_P, _I, _IP, _IP, _IP, _IP, _IP, _IP, _IP, _IP, _IP]),
     "sgf_plan_footprint": (_I, [_P, _SZP, _SZP]),
+    "sgf_plan_get_tuning": (_I, [_P, C.POINTER(sgf_tuning)]),
+    "sgf_plan_set_tuning": (_I, [_P, C.POINTER(sgf_tuning)]),
+    "sgf_autotune": (_I, [_P, _P, _P, _I, C.POINTER(sgf_tuning), C.POINTER(C.c_double)]),
     "sgf_factor": (_I, [_P, _P, _P, C.POINTER(_P)]),
     "sgf_factor_destroy": (None, [_P]),
     "sgf_factor_level_stats": (_I, [_P, _I, _IP, _I64P, _I64P, _I64P]),

@@ -108,12 +108,95 @@ int sgf_plan_footprint(const sgf_plan* plan, size_t* b64, size_t* bmx) {
   for (size_t li = 0; li < P.lev.size(); ++li) {
     sgf::LevelLayout lay;
     sgf::build_layout(P.lev[li], P.mcap[li], lay);
-    words += 3.0 * lay.dg_size + 2.0 * lay.up_size + 3.0 * lay.vec_size + P.pi * lay.vec_size;
+    // diagonal blocks (A, L, L^{-1}), panels (A, W, W^T), level vectors, Phi
+    words += 3.0 * lay.dg_size + 3.0 * lay.up_size + 3.0 * lay.vec_size + P.pi * lay.vec_size;
   }
   const double extra = 64.0 * P.npts;  // stencil arrays, maps, vectors
   if (b64) *b64 = (size_t)(8.0 * words + extra);
   if (bmx) *bmx = (size_t)(4.0 * words + extra);
   return SGF_OK;
+}
+
+int sgf_plan_get_tuning(const sgf_plan* plan, sgf_tuning* out) {
+  if (!plan || !out) return SGF_ERR_INVALID_ARG;
+  *out = plan->p.tune;
+  return SGF_OK;
+}
+
+int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t) {
+  if (!plan || !t || !sgf::tuning_valid(*t)) return SGF_ERR_INVALID_ARG;
+  plan->p.tune = *t;
+  return SGF_OK;
+}
+
+// Grid search over launch shapes: each candidate is timed on one factorization
+// plus napply applications of A_l^{-1}, the fastest is kept.
+int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int napply, sgf_tuning* best,
+                 double* best_ms) {
+  if (!plan || !coeffs_dev || napply < 0) return SGF_ERR_INVALID_ARG;
+  if (sgf::dry_run()) return SGF_ERR_UNSUPPORTED;
+  const sgf_tuning saved = plan->p.tune;
+  const int rc = guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool mixed = plan->p.opts.precision == SGF_PREC_MIXED;
+    std::vector<sgf_tuning> cand;
+    const int budgets[3][2] = {{4096, 32768}, {8192, 65536}, {16384, 131072}};
+    for (const auto& bgt : budgets) {
+      if (mixed) {
+        for (int tc : {1, 0})
+          for (int fs : {512, 256}) cand.push_back({bgt[0], bgt[1], fs, tc});
+      } else {
+        cand.push_back({bgt[0], bgt[1], saved.front_small, saved.tensor_cores});
+      }
+    }
+    const int64_t n = plan->p.n;
+    double* x = (double*)sgf::dev_malloc(sizeof(double) * n);
+    double* y = (double*)sgf::dev_malloc(sizeof(double) * n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SGF_CK(cudaEventCreate(&e0));
+    SGF_CK(cudaEventCreate(&e1));
+    struct Cleanup {
+      double *x, *y;
+      cudaEvent_t a, b;
+      ~Cleanup() {
+        sgf::dev_free(x);
+        sgf::dev_free(y);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+      }
+    } cleanup{x, y, e0, e1};
+    sgf::dev_memset(x, 0, sizeof(double) * n, s);   // any fixed vector times the same
+    {
+      plan->p.tune = cand[0];   // warm-up: caches, pools, module loading
+      auto f = sgf::make_factor(plan->p, coeffs_dev, s);
+      if (napply > 0) f->apply(x, y, s);
+      sgf::dev_sync(s);
+    }
+    double best_t = 1e300;
+    sgf_tuning best_c = saved;
+    for (const sgf_tuning& c : cand) {
+      plan->p.tune = c;
+      SGF_CK(cudaEventRecord(e0, s));
+      {
+        auto f = sgf::make_factor(plan->p, coeffs_dev, s);
+        for (int k = 0; k < napply; ++k) f->apply(x, y, s);
+        SGF_CK(cudaEventRecord(e1, s));
+        SGF_CK(cudaEventSynchronize(e1));
+      }
+      float ms = 0;
+      SGF_CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_t) {
+        best_t = ms;
+        best_c = c;
+      }
+    }
+    plan->p.tune = best_c;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return (int)SGF_OK;
+  });
+  if (rc != SGF_OK) plan->p.tune = saved;
+  return rc;
 }
 
 int sgf_factor(const sgf_plan* plan, const double* coeffs_dev, void* stream, sgf_factor_t** out) {

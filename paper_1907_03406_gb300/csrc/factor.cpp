@@ -158,6 +158,19 @@ void Batch::release(cudaStream_t s) {
 
 namespace {
 
+// Launch shapes of the factorization or program build running on this thread
+// (the plan's sgf_tuning), set for its duration by TuneScope.
+thread_local const sgf_tuning* t_tune = nullptr;
+struct TuneScope {
+  const sgf_tuning* prev;
+  explicit TuneScope(const sgf_tuning* t) : prev(t_tune) { t_tune = t; }
+  ~TuneScope() { t_tune = prev; }
+};
+inline const sgf_tuning& active_tuning() {
+  static const sgf_tuning def{4096, 32768, 512, 1};
+  return t_tune ? *t_tune : def;
+}
+
 // Vectors handed out with the capacity they reached in earlier use on this
 // thread (task lists are rebuilt for every factorization; growing them from
 // empty each time costs reallocation copies).
@@ -208,7 +221,7 @@ struct GemmList {
   std::vector<GemmTask<T>>& t = tp.v;
   std::vector<GemmContrib<T>>& c = cp.v;
   // FP32 products go to the tensor cores (3xTF32) in kTileTC-row tiles
-  const bool tc = std::is_same<T, float>::value && gemm_tc_enabled();
+  const bool tc = std::is_same<T, float>::value && gemm_tc_enabled() && active_tuning().tensor_cores;
   const int tm = tc ? kTileTC : kTile;
   void add(T* C, int ldc, int M, int N, T alpha, int beta, std::initializer_list<Spec<T>> specs) {
     add_range(C, ldc, M, N, alpha, beta, specs.begin(), specs.end());
@@ -356,7 +369,7 @@ void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, Dev
   // front_small the tile sweep spread over many CTAs wins (one CTA pays a
   // memory latency per tile product), and so it does for fronts above
   // kFrontTiny when the batch holds too few of them to occupy every SM.
-  constexpr int small_max = front_small<T>();
+  const int small_max = std::is_same<T, float>::value ? active_tuning().front_small : front_small<T>();
   int nfit = 0;
   for (const auto& f : Fall)
     if (f.s == 0 && f.m <= small_max) ++nfit;
@@ -473,11 +486,10 @@ struct Program {
 };
 
 // Element budget of one GEMV task (one CTA): the launch's elements spread
-// over about eight CTAs per SM, kept between 4K and 32K elements (small
-// launches get more, shorter tasks; large ones long enough to hide the
-// start-up latency).
+// over about eight CTAs per SM, kept within the tuning's range (by default 4K
+// to 32K elements: small launches get more, shorter tasks; large ones long
+// enough to hide the start-up latency).
 constexpr double kGemvCtas = 152.0 * 8.0;
-constexpr double kGemvMinElems = 4096.0, kGemvMaxElems = 32768.0;
 
 template <typename T>
 struct GemvList {
@@ -620,7 +632,8 @@ struct GemvList {
         by += (double)sizeof(T) * (el + (double)c[k].K * nr * (c[k].x2 ? 2.0 : 1.0));
       }
     }
-    const double budget = std::min(kGemvMaxElems, std::max(kGemvMinElems, el_all / kGemvCtas));
+    const sgf_tuning& tu = active_tuning();
+    const double budget = std::min((double)tu.gemv_max_elems, std::max((double)tu.gemv_min_elems, el_all / kGemvCtas));
     std::vector<GemvTask<T>> tasks;
     size_t npart = 0;
     int ncnt = 0;
@@ -676,6 +689,7 @@ class FactorImpl final : public FactorBase {
   FactorImpl(const Plan& P, const double* coeffs, cudaStream_t s) {
     plan = &P;
     n = P.n;
+    tune_ = P.tune;   // a factor keeps the launch shapes it was made with
     st_ = (DevStatus*)dev_malloc(sizeof(DevStatus));
     dev_memset(st_, 0, sizeof(DevStatus), s);
     try {
@@ -720,6 +734,7 @@ class FactorImpl final : public FactorBase {
   std::vector<T*> vb_;  // per non-top level: [v | w | kept], 3 * vec_size
   T* vtop_ = nullptr;   // [v | w], 2 * mtop
   Program<T> inv_[4], fwd_[4];   // nr = 1, 2, 4, 8 right-hand sides, built on first use
+  sgf_tuning tune_{};
   std::mutex prog_mu_;
 
   void release() {
@@ -860,6 +875,7 @@ class FactorImpl final : public FactorBase {
 
   void build(const double* coeffs, cudaStream_t s) {
     const Plan& P = *plan;
+    TuneScope tscope(&tune_);
     trace(s, 0, "start");
     const int pi = P.pi;
     Batch b;
@@ -1377,6 +1393,7 @@ class FactorImpl final : public FactorBase {
     const int k = nr == 1 ? 0 : nr == 2 ? 1 : nr == 4 ? 2 : 3;
     Program<T>& P = inverse ? inv_[k] : fwd_[k];
     if (P.ops.empty()) {
+      TuneScope tscope(&tune_);
       if (inverse) build_inverse(P, nr, s);
       else build_forward(P, nr, s);
       P.b.upload_persistent(s);

@@ -73,6 +73,8 @@ struct Plan {
   // vector slot
   std::vector<int64_t> asm_map, perm1;
   std::vector<int> asm_ld;         // Q1: level-1 node size of every point
+  // launch shapes (sgf_tuning; see sgf_plan_set_tuning)
+  sgf_tuning tune{4096, 32768, 512, 1};
 
   // device copies of the plan's constant data, built on first use
   struct DevCache {
@@ -212,6 +214,8 @@ struct GemvContrib {
 // for a dense block; for a lower-triangular one the columns j <= last row (op
 // N) or the rows i >= first column (op T); for an upper-triangular one (op T)
 // the rows i <= last column.
+bool tuning_valid(const sgf_tuning& t);
+
 SGF_HD inline void gemv_useful(bool trans, int tri, int upper, int K, int M, int* kb, int* ke) {
   if (!tri) {
     *kb = 0;

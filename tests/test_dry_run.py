@@ -23,10 +23,13 @@ import paper_1907_03406_gb300 as sgf
 from paper_1907_03406_gb300 import _lib
 lib = _lib.load()
 out = []
-for (n, dim, st, dm, leaf, deg, prec, scheme) in json.loads(sys.argv[1]):
+for case in json.loads(sys.argv[1]):
+    (n, dim, st, dm, leaf, deg, prec, scheme) = case[:8]
     el = st == "q1_elastic_3d"
     P = sgf.Plan(tuple(n), dim, st, dm, leaf, deg, precision=prec, scheme=scheme,
                  basis=1 if el else 0, dof=3 if el else 1)
+    if len(case) > 8:
+        P.tuning = case[8]      # non-default launch shapes
     lib.sgf_dry_run_violations(1)
     h = C.c_void_p()
     rc = lib.sgf_factor(P.handle, C.c_void_p(4096), None, C.byref(h))
@@ -55,6 +58,10 @@ CASES = [
     [[130, 67, 1], 2, "5pt_2d", 15, 8, 2, "mixed", "nest_all_all"],
     [[12, 13, 13], 3, "q1_elastic_3d", 1, 4, 1, "fp64", "nest_all_all"],
     [[24, 25, 25], 3, "q1_elastic_3d", 1, 8, 1, "mixed", "nest_all_all"],
+    [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "mixed", "nest_all_all",
+     {"gemv_min_elems": 256, "gemv_max_elems": 1024, "front_small": 64, "tensor_cores": 0}],
+    [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "fp64", "nest_all_all",
+     {"gemv_min_elems": 65536, "gemv_max_elems": 1 << 20, "front_small": 512, "tensor_cores": 1}],
 ]
 
 

@@ -270,3 +270,22 @@ def test_rigid_body_modes_preserved_on_gpu(name, precision):
     bvec = _t(si.rhs(plan.n, 0))
     x, info = F.pcg(bvec, rtol=1e-10, maxit=1000)
     assert info["rel_residual"] <= 1e-10
+
+
+@pytest.mark.gpu
+def test_autotune_keeps_a_valid_tuning_and_the_solution():
+    # the autotuner only changes launch shapes: the tuned plan solves to the
+    # same tolerance in the same number of iterations (+-1)
+    cfg = _problem("grf3d_16")
+    plan, F = _gpu(cfg, precision="mixed")
+    b = _t(si.rhs(plan.n, 0))
+    _, info0 = F.pcg(b, rtol=1e-10, maxit=500)
+    F.close()
+    best, ms = plan.autotune(_t(cfg["coeffs"].ravel()), napply=3)
+    assert ms > 0 and plan.tuning == best
+    assert best["tensor_cores"] in (0, 1) and 64 <= best["front_small"] <= 512
+    F2 = sgf.Factor(plan, _t(cfg["coeffs"].ravel()))
+    _, info1 = F2.pcg(b, rtol=1e-10, maxit=500)
+    assert info1["rel_residual"] <= 1e-10
+    assert abs(info1["iterations"] - info0["iterations"]) <= 1
+    F2.close()
