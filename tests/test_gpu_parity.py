@@ -289,3 +289,32 @@ def test_autotune_keeps_a_valid_tuning_and_the_solution():
     assert info1["rel_residual"] <= 1e-10
     assert abs(info1["iterations"] - info0["iterations"]) <= 1
     F2.close()
+
+
+@pytest.mark.slow
+def test_full_size_128cube_two_phase_properties():
+    # 128^3 high-contrast workload at full size, in the configuration the
+    # bench and the examples run: properties that hold at any size - the FP64
+    # factor reproduces A on the quadratics (Eq. (preserve-pi)), both
+    # precisions reach the 1e-10 residual, and the mixed-precision
+    # preconditioner needs about as many iterations as the FP64 one
+    cfg = _problem("twophase3d_128")
+    e = cfg["n"][0]
+    b = _t(si.rhs(e ** 3, 0))
+    its = {}
+    for precision in ("fp64", "mixed"):
+        plan, F = _gpu(cfg, precision=precision)
+        if precision == "fp64":
+            p = np.arange(plan.n)
+            xyz = np.stack([p % e, (p // e) % e, p // (e * e)], 1).astype(float)
+            Pi = eval_monomials(xyz, exponents(3, 2))
+            for k in range(Pi.shape[1]):
+                v = _t(Pi[:, k])
+                a, r = F.apply_forward(v), F.spmv(v)
+                assert torch.linalg.norm(a - r).item() <= 1e-10 * torch.linalg.norm(r).item()
+        x, info = F.pcg(b, rtol=1e-10, maxit=1000)
+        assert info["rel_residual"] <= 1e-10
+        its[precision] = info["iterations"]
+        F.close()
+    print(f"128^3 two-phase PCG iterations: {its}")
+    assert its["mixed"] <= 1.3 * its["fp64"]
