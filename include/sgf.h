@@ -183,6 +183,11 @@ int sgf_factor_level_stats(const sgf_factor_t* f, int level, int* ncompressed,
 int sgf_factor_ranks(const sgf_factor_t* f, int level, int* m, int* r);
 /* Last device status: node index of a failed pivot (or -1) and status.     */
 int sgf_factor_status(const sgf_factor_t* f, int* bad_level, int* bad_node);
+/* Precision the factor holds: SGF_PREC_FP64 or SGF_PREC_MIXED.  A mixed
+ * request whose FP32 factorization met a non-positive or non-finite pivot is
+ * factored again entirely in FP64 (the mixed-precision policy: CG then runs
+ * on an FP64 preconditioner); it reports SGF_PREC_FP64.  -1 on NULL.       */
+int sgf_factor_precision(const sgf_factor_t* f);
 
 /* ---- apply (Sec. 4.7) and products ----------------------------------------
  * y = A_l^{-1} x (sgf_apply) or y = A_l x (sgf_apply_forward); nrhs vectors,

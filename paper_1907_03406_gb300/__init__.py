@@ -166,6 +166,11 @@ class Factor:
         _check(fn(self.handle, _dev_ptr(x), _dev_ptr(out), nrhs, _stream_ptr(stream)), fn.__name__)
         return out
 
+    @property
+    def precision(self) -> str:
+        """"mixed", or "fp64" (also when a mixed request fell back to FP64)."""
+        return "mixed" if self._lib.sgf_factor_precision(self.handle) == 1 else "fp64"
+
     def apply(self, x, out=None, stream=None):
         """A_l^{-1} x."""
         return self._vec_call(self._lib.sgf_apply, x, out, stream)

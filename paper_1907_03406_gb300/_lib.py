@@ -45,6 +45,7 @@ SIGNATURES = {
     "sgf_plan_export_level": (_I, [_P, _I, _IP, _IP, _IP, _IP, _IP, _IP, _IP, _IP, _IP]),
     "sgf_plan_footprint": (_I, [_P, _SZP, _SZP]),
     "sgf_plan_get_tuning": (_I, [_P, C.POINTER(sgf_tuning)]),
+    "sgf_factor_precision": (_I, [_P]),
     "sgf_plan_set_tuning": (_I, [_P, C.POINTER(sgf_tuning)]),
     "sgf_autotune": (_I, [_P, _P, _P, _I, C.POINTER(sgf_tuning), C.POINTER(C.c_double)]),
     "sgf_factor": (_I, [_P, _P, _P, C.POINTER(_P)]),

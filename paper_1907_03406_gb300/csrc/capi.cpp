@@ -233,6 +233,11 @@ int sgf_factor_ranks(const sgf_factor_t* f, int level, int* m, int* r) {
   return SGF_OK;
 }
 
+int sgf_factor_precision(const sgf_factor_t* f) {
+  if (!f) return -1;
+  return f->f->mixed() ? SGF_PREC_MIXED : SGF_PREC_FP64;
+}
+
 int sgf_factor_status(const sgf_factor_t* f, int* bl, int* bn) {
   if (!f) return SGF_ERR_INVALID_ARG;
   if (bl) *bl = f->f->bad_level;

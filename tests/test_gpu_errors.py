@@ -52,3 +52,27 @@ def test_maxit_reports_no_convergence():
     b = torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=DEV)
     x, info = F.pcg(b, rtol=1e-10, maxit=2, check=False)
     assert info["status"] == -5 and info["iterations"] == 2
+
+
+def test_mixed_falls_back_to_fp64_when_an_fp32_pivot_fails():
+    # an SPD field with a 1e12 inclusion: the FP32 Cholesky of the blocks
+    # around it loses the inclusion's weak coupling to rounding (relative
+    # 1e-12 < eps32) and meets a non-positive pivot, FP64 does not; the mixed
+    # request is refactored in FP64 and solves as well as an FP64 plan (at this
+    # contrast the attainable true residual is ~eps64 cond(A) ~ 1e-4, for both)
+    cfg = si.config("grf3d_16")
+    k = np.ones_like(cfg["coeffs"])
+    k[2:6, 2:6, 2:6] = 1e12
+    b = torch.tensor(si.rhs(int(np.prod(cfg["n"])), 0), dtype=torch.float64, device=DEV)
+    plan64 = sgf.Plan.from_config(cfg, precision="fp64")
+    F64 = sgf.Factor(plan64, _coeffs(k))
+    assert F64.precision == "fp64"
+    _, info64 = F64.pcg(b, rtol=1e-10, maxit=500, check=False)
+    plan = sgf.Plan.from_config(cfg, precision="mixed")
+    F = sgf.Factor(plan, _coeffs(k))
+    assert F.precision == "fp64"          # the FP32 attempt failed, FP64 was used
+    _, info = F.pcg(b, rtol=1e-10, maxit=500, check=False)
+    assert info["rel_residual"] <= 10 * info64["rel_residual"]
+    assert abs(info["iterations"] - info64["iterations"]) <= 2
+    F_ok = sgf.Factor(plan, _coeffs(cfg["coeffs"]))
+    assert F_ok.precision == "mixed"      # an ordinary field stays in FP32
