@@ -17,6 +17,14 @@ of S_t, every level-t cell lies in one level-(t+1) cell (Def. 2.2).
 
 The top level is the first one with no separator on any axis; it has one node.
 
+General partitions (Sec. 5.2, the Gen-All-All scheme): every level-t cell is a
+box of d = b * 2^(t-1) consecutive grid vertices per axis, [k d, (k+1) d - 1]
+(the last one clipped to the grid), so the level-t cell holds (b 2^(t-1))^3
+vertices; there are no separators and no interiors, every node is of full
+dimension, and the 2 x 2 x 2 level-t cells of a level-(t+1) cell are its
+children.  The top is the first level with a single cell.  Codes are 2k per
+axis (the same encoding as intervals above).
+
 Canonical node order within a level: interiors first, then separators, each
 group sorted by the cell code tuple (z, y, x).  The active variables of a
 level-1 node are its points' DOFs in natural order; those of a level-(t+1)
@@ -108,6 +116,7 @@ class Hierarchy:
     dof: int
     stencil: str
     levels: list
+    general: bool = False   # general partitions (no interiors)
 
 
 def _sort_nodes(codes_list, interior_list):
@@ -116,8 +125,9 @@ def _sort_nodes(codes_list, interior_list):
     return keyed
 
 
-def build_hierarchy(n, dim: int, leaf: int, stencil: str, dof: int = 1) -> Hierarchy:
-    """Build P_1 < P_2 < ... < P_l with node orders, children and block patterns."""
+def build_hierarchy(n, dim: int, leaf: int, stencil: str, dof: int = 1, general: bool = False) -> Hierarchy:
+    """Build P_1 < P_2 < ... < P_l with node orders, children and block patterns
+    (nested dissection, or general partitions when `general`)."""
     nx, ny, nz = (list(n) + [1, 1, 1])[:3]
     if dim == 2:
         nz = 1
@@ -131,8 +141,12 @@ def build_hierarchy(n, dim: int, leaf: int, stencil: str, dof: int = 1) -> Hiera
     prev_point_node = None
     while True:
         d = leaf * 2 ** (t - 1)
-        seps = [axis_separators(N[a], d) if N[a] > 1 else [] for a in range(3)]
-        top = all(len(s) == 0 for s in seps)
+        if general:
+            seps = [[], [], []]
+            top = all(-(-N[a] // d) == 1 for a in range(3))
+        else:
+            seps = [axis_separators(N[a], d) if N[a] > 1 else [] for a in range(3)]
+            top = all(len(s) == 0 for s in seps)
         if top:
             lev = Level(t=t, d=d, seps=seps, codes=[(0, 0, 0)], interior=np.array([False]),
                         cell_dim=np.array([dim]),
@@ -143,9 +157,12 @@ def build_hierarchy(n, dim: int, leaf: int, stencil: str, dof: int = 1) -> Hiera
                 lev.children = [[i for i in range(prev.nnodes) if not prev.interior[i]]]
             levels.append(lev)
             break
-        cx = axis_codes(nx, seps[0])
-        cy = axis_codes(ny, seps[1])
-        cz = axis_codes(nz, seps[2])
+        if general:
+            cx, cy, cz = (2 * (np.arange(N[a]) // d) for a in range(3))
+        else:
+            cx = axis_codes(nx, seps[0])
+            cy = axis_codes(ny, seps[1])
+            cz = axis_codes(nz, seps[2])
         # every cell is the product of per-axis codes
         all_codes = []
         ux, uy, uz = sorted(set(cx.tolist())), sorted(set(cy.tolist())), sorted(set(cz.tolist()))
@@ -153,17 +170,20 @@ def build_hierarchy(n, dim: int, leaf: int, stencil: str, dof: int = 1) -> Hiera
             for cyv in uy:
                 for cxv in ux:
                     all_codes.append((czv, cyv, cxv))
-        interior_flags = [all(c % 2 == 0 for c in code) for code in all_codes]
+        interior_flags = [(not general) and all(c % 2 == 0 for c in code) for code in all_codes]
         order = _sort_nodes(all_codes, interior_flags)
         codes = [all_codes[i] for i in order]
         interior = np.array([interior_flags[i] for i in order])
         cell_dim = np.array([sum(1 for a, c in enumerate(code[::-1]) if a < dim and c % 2 == 0)
-                             for code in codes])
+                             for code in codes])   # = dim for every general cell
         index = {c: i for i, c in enumerate(codes)}
         box = np.zeros((len(codes), 2, 3), dtype=np.int64)
         for i, (czv, cyv, cxv) in enumerate(codes):
             for a, cv in enumerate((cxv, cyv, czv)):
-                lo, hi = code_extent(N[a], seps[a], cv)
+                if general:
+                    lo, hi = (cv // 2) * d, min((cv // 2 + 1) * d, N[a]) - 1
+                else:
+                    lo, hi = code_extent(N[a], seps[a], cv)
                 box[i, 0, a], box[i, 1, a] = lo, hi
         lev = Level(t=t, d=d, seps=seps, codes=codes, interior=interior, cell_dim=cell_dim, box=box)
         # node of each point at this level
@@ -186,7 +206,7 @@ def build_hierarchy(n, dim: int, leaf: int, stencil: str, dof: int = 1) -> Hiera
         prev = lev
         prev_point_node = point_node
         t += 1
-    H = Hierarchy(n=N, dim=dim, leaf=leaf, dof=dof, stencil=stencil, levels=levels)
+    H = Hierarchy(n=N, dim=dim, leaf=leaf, dof=dof, stencil=stencil, levels=levels, general=general)
     _patterns(H, px, py, pz)
     return H
 

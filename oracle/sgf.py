@@ -31,7 +31,9 @@ Readings (the paper leaves these open):
 * tau = 1e-12 relative to |R_11| (the paper only says "e.g. pivoted QR");
 * 0-cells are never compressed (Sec. 5.1 notes it makes no difference);
 * Nest-2-All compresses only separators of codimension 1;
-* scheme "none" disables compression, which gives exact block Cholesky.
+* scheme "none" disables compression, which gives exact block Cholesky;
+* Gen-All-All (Sec. 5.2) runs on general partitions
+  (build_hierarchy(general=True)): no interiors, every node is compressed.
 """
 from __future__ import annotations
 
@@ -46,7 +48,7 @@ from .partition import Hierarchy
 
 @dataclass
 class Options:
-    scheme: str = "nest_all_all"     # "nest_all_all" | "nest_2_all" | "none"
+    scheme: str = "nest_all_all"     # "nest_all_all" | "nest_2_all" | "gen_all_all" | "none"
     tau: float = 1e-12
     compress_from_level: int = 1
     basis: str = "poly"              # "poly" | "rbm"
@@ -66,6 +68,8 @@ def _eligible(lev, i, dim, opts: Options) -> bool:
         return cd >= 1
     if opts.scheme == "nest_2_all":
         return cd == dim - 1
+    if opts.scheme == "gen_all_all":   # Sec. 5.2: every node of a general partition
+        return True
     raise ValueError(opts.scheme)
 
 

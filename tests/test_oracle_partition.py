@@ -107,3 +107,35 @@ def test_local_basis_spans_global_monomials():
     glo = eval_monomials(xyz, exponents(3, 2))
     X, *_ = np.linalg.lstsq(loc, glo, rcond=None)
     assert np.abs(loc @ X - glo).max() < 1e-9 * np.abs(glo).max()
+
+
+@pytest.mark.parametrize("n,dim,b", [((20, 18, 16), 3, 4), ((23, 19, 1), 2, 5), ((15, 15, 15), 3, 5)])
+def test_general_partition_cells(n, dim, b):
+    # Gen-All-All partitions (Sec. 5.2): level t has ceil(N / d) cells per axis
+    # of d = b 2^(t-1) consecutive vertices, none interior, all of full
+    # dimension; every point lies in one level-1 cell; a cell's children are
+    # the level-(t-1) cells inside it; the top is the first single-cell level
+    H = build_hierarchy(n, dim, b, "7pt_fv_3d" if dim == 3 else "5pt_2d", general=True)
+    N = [n[0], n[1], n[2] if dim == 3 else 1]
+    npts = N[0] * N[1] * N[2]
+    assert sorted(np.concatenate(H.levels[0].points).tolist()) == list(range(npts))
+    for li, lev in enumerate(H.levels):
+        d = b * 2 ** li
+        K = [-(-N[a] // d) if N[a] > 1 else 1 for a in range(3)]
+        if lev.top:
+            assert lev.nnodes == 1 and all(k == 1 for k in K)
+            continue
+        assert lev.nnodes == K[0] * K[1] * K[2]
+        assert not lev.interior.any() and (lev.cell_dim == dim).all()
+        sizes = [(lev.box[i, 1] - lev.box[i, 0] + 1) for i in range(lev.nnodes)]
+        for sz in sizes:
+            assert all(1 <= sz[a] <= d for a in range(3))
+        if li == 0:
+            assert [len(p) for p in lev.points] == [int(np.prod(sz)) for sz in sizes]
+        else:
+            prev = H.levels[li - 1]
+            for D, kids in enumerate(lev.children):
+                assert 1 <= len(kids) <= 2 ** dim
+                for c in kids:   # child box inside the parent box
+                    assert (prev.box[c, 0] >= lev.box[D, 0]).all() and (prev.box[c, 1] <= lev.box[D, 1]).all()
+            assert sorted(c for k in lev.children for c in k) == list(range(prev.nnodes))

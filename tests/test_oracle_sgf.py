@@ -24,14 +24,14 @@ from oracle.pcg import pcg
 from oracle.sgf import Options, factorize, dof_list
 
 
-def _grid_problem(n, dim, b, stencil, seed=0, weight=1.0, dmask=None):
+def _grid_problem(n, dim, b, stencil, seed=0, weight=1.0, dmask=None, general=False):
     rng = np.random.default_rng(seed)
     shape = (n[1], n[0]) if dim == 2 else (n[2], n[1], n[0])
     k = np.exp(rng.standard_normal(shape))
     if dmask is None:
         dmask = 15 if dim == 2 else 1
     A = assemble_scalar(n, dim, k, dmask, weight)
-    H = build_hierarchy(n, dim, b, stencil)
+    H = build_hierarchy(n, dim, b, stencil, general=general)
     return A, H
 
 
@@ -233,3 +233,41 @@ def test_pcg_finite_termination_and_exact_preconditioner():
     x1, it1, _ = pcg(lambda v: A @ v, lambda v: v / ev.mean(), b, flexible=True)
     x2, it2, _ = pcg(lambda v: A @ v, lambda v: v / ev.mean(), b, flexible=False)
     assert it1 == it2 and np.allclose(x1, x2, rtol=1e-8)
+
+
+# ---- Gen-All-All (Sec. 5.2): general partitions, compression only --------
+
+@pytest.mark.parametrize("n,dim,b", [((17, 15, 1), 2, 4), ((10, 9, 8), 3, 3)])
+def test_gen_P1_no_compression_is_exact(n, dim, b):
+    # without interiors and without compression nothing happens before the
+    # top level, whose dense Cholesky is exact: A_l = A
+    A, H = _grid_problem(n, dim, b, "5pt_2d" if dim == 2 else "7pt_fv_3d", seed=1, general=True)
+    F = factorize(A, H, Options(scheme="none", degree=1))
+    Al = F.dense_operator()
+    Ad = A.toarray()
+    assert np.abs(Al - Ad).max() <= 1e-12 * np.abs(Ad).max()
+
+
+@pytest.mark.parametrize("n,dim,b,deg", [((24, 21, 1), 2, 4, 1), ((16, 15, 14), 3, 4, 1), ((20, 20, 20), 3, 5, 2)])
+def test_gen_P2_P4_preserves_polynomials_and_stays_spd(n, dim, b, deg):
+    A, H = _grid_problem(n, dim, b, "5pt_2d" if dim == 2 else "7pt_fv_3d", seed=2, general=True)
+    F = factorize(A, H, Options(scheme="gen_all_all", degree=deg))
+    assert F.pivots_min > 0
+    assert any(v[2] for v in F.ranks().values()), "some node must actually compress"
+    Pi = _global_poly(H, deg)
+    AP = A @ Pi
+    err = np.linalg.norm(np.stack([F.multiply(Pi[:, k]) for k in range(Pi.shape[1])], 1) - AP)
+    assert err <= 1e-12 * np.linalg.norm(AP)
+
+
+@pytest.mark.parametrize("n,seed,deg", [((20, 17, 1), 0, 0), ((23, 19, 1), 3, 1)])
+def test_gen_P5_dense_brute_force_reproduces_block_oracle(n, seed, deg):
+    A, H = _grid_problem(n, 2, 4, "5pt_2d", seed=seed, general=True)
+    opts = Options(scheme="gen_all_all", degree=deg)
+    F = factorize(A, H, opts)
+    Ad, _, ranks = dense_sgf(A, H, opts)
+    assert ranks == F.ranks()
+    assert any(v[2] for v in ranks.values())
+    Al = F.dense_operator()
+    assert np.abs(Al - Ad).max() <= 1e-12 * np.abs(Ad).max()
+    assert np.linalg.eigvalsh(0.5 * (Ad + Ad.T))[0] > 0
