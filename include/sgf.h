@@ -74,7 +74,10 @@ typedef struct sgf_grid {
 typedef enum {
   SGF_SCHEME_NEST_ALL_ALL = 0, /* every separator cell of dimension >= 1      */
   SGF_SCHEME_NEST_2_ALL = 1,   /* codimension-1 separators only               */
-  SGF_SCHEME_NONE = 2          /* no compression: exact block Cholesky        */
+  SGF_SCHEME_NONE = 2,         /* no compression: exact block Cholesky        */
+  SGF_SCHEME_GEN_ALL_ALL = 3   /* general partitions (Sec. 5.2): cells of      */
+                               /* (b 2^(t-1))^3 vertices, no interiors, every  */
+                               /* node compressed                              */
 } sgf_scheme;
 
 typedef enum { SGF_BASIS_POLY = 0, SGF_BASIS_RBM = 1 } sgf_basis;

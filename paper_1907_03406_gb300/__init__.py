@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib as L
 
 STENCILS = {"5pt_2d": 0, "7pt_3d": 1, "7pt_fv_3d": 2, "q1_elastic_3d": 3}
-SCHEMES = {"nest_all_all": 0, "nest_2_all": 1, "none": 2}
+SCHEMES = {"nest_all_all": 0, "nest_2_all": 1, "none": 2, "gen_all_all": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 OK = 0
@@ -85,6 +85,7 @@ class Plan:
     def from_config(cls, cfg: dict, **kw):
         kw.setdefault("basis", 1 if cfg.get("basis") == "rbm" else 0)
         kw.setdefault("dof", cfg.get("dof", 1))
+        kw.setdefault("scheme", cfg.get("scheme", "nest_all_all"))
         if "nu" in cfg:
             kw.setdefault("nu", cfg["nu"])
         return cls(cfg["n"], cfg["dim"], cfg["stencil"], cfg["dirichlet"], cfg["leaf"],

@@ -291,7 +291,8 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
   if (op->leaf < 2) { err = "leaf must be >= 2"; return SGF_ERR_INVALID_ARG; }
   if (op->degree < 0 || op->degree > 2) { err = "degree must be 0, 1 or 2"; return SGF_ERR_INVALID_ARG; }
   if (!elastic && op->basis != SGF_BASIS_POLY) { err = "scalar problems use the polynomial basis"; return SGF_ERR_UNSUPPORTED; }
-  if (op->scheme < 0 || op->scheme > 2) { err = "bad scheme"; return SGF_ERR_INVALID_ARG; }
+  if (op->scheme < 0 || op->scheme > 3) { err = "bad scheme"; return SGF_ERR_INVALID_ARG; }
+  const bool general = op->scheme == SGF_SCHEME_GEN_ALL_ALL;
   if (op->precision != SGF_PREC_FP64 && op->precision != SGF_PREC_MIXED) { err = "bad precision"; return SGF_ERR_INVALID_ARG; }
 
   P.grid = *g;
@@ -320,9 +321,15 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
     L.d = dd > (1 << 30) ? (1 << 30) : (int)dd;
     std::vector<int> seps[3];
     bool any = false;
+    int KG[3] = {1, 1, 1};   // general partitions: cells per axis
     for (int a = 0; a < 3; ++a) {
-      if (N[a] > 1) seps[a] = axis_separators(N[a], L.d);
-      any = any || !seps[a].empty();
+      if (general) {
+        if (N[a] > 1) KG[a] = (N[a] + L.d - 1) / L.d;
+        any = any || KG[a] > 1;
+      } else {
+        if (N[a] > 1) seps[a] = axis_separators(N[a], L.d);
+        any = any || !seps[a].empty();
+      }
     }
     if (!any) {
       L.top = true;
@@ -346,18 +353,38 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
       P.lev.push_back(std::move(L));
       break;
     }
-    std::vector<int> cx = axis_codes(P.nx, seps[0]), cy = axis_codes(P.ny, seps[1]),
-                     cz = axis_codes(P.nz, seps[2]);
-    const int KX = 2 * (int)seps[0].size() + 1, KY = 2 * (int)seps[1].size() + 1,
-              KZ = 2 * (int)seps[2].size() + 1;
+    std::vector<int> cx, cy, cz;
+    int KX, KY, KZ;
+    if (general) {   // code 2k for the k-th run of d vertices (no separator codes)
+      auto gcodes = [&](int n) {
+        std::vector<int> c(n);
+        for (int i = 0; i < n; ++i) c[i] = 2 * (i / L.d);
+        return c;
+      };
+      cx = gcodes(P.nx);
+      cy = gcodes(P.ny);
+      cz = gcodes(P.nz);
+      KX = 2 * KG[0] - 1;
+      KY = 2 * KG[1] - 1;
+      KZ = 2 * KG[2] - 1;
+    } else {
+      cx = axis_codes(P.nx, seps[0]);
+      cy = axis_codes(P.ny, seps[1]);
+      cz = axis_codes(P.nz, seps[2]);
+      KX = 2 * (int)seps[0].size() + 1;
+      KY = 2 * (int)seps[1].size() + 1;
+      KZ = 2 * (int)seps[2].size() + 1;
+    }
     // enumerate cells, sort interiors first then by (z, y, x) code
     struct Cell { int z, y, x; bool in; };
     std::vector<Cell> cells;
     cells.reserve((size_t)KX * KY * KZ);
     for (int z = 0; z < KZ; ++z)
       for (int y = 0; y < KY; ++y)
-        for (int x = 0; x < KX; ++x)
-          cells.push_back({z, y, x, (x % 2 == 0) && (y % 2 == 0) && (z % 2 == 0)});
+        for (int x = 0; x < KX; ++x) {
+          if (general && (x % 2 || y % 2 || z % 2)) continue;   // no separator cells
+          cells.push_back({z, y, x, !general && (x % 2 == 0) && (y % 2 == 0) && (z % 2 == 0)});
+        }
     std::stable_sort(cells.begin(), cells.end(), [](const Cell& a, const Cell& b) {
       if (a.in != b.in) return a.in;
       if (a.z != b.z) return a.z < b.z;
@@ -381,11 +408,19 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
       int cd = (c.x % 2 == 0) + (c.y % 2 == 0) + (dim == 3 ? (c.z % 2 == 0) : 0);
       L.cell_dim[i] = cd;
       const int cc[3] = {c.x, c.y, c.z};
-      for (int a = 0; a < 3; ++a) code_extent(N[a], seps[a], cc[a], L.box[6 * i + a], L.box[6 * i + 3 + a]);
+      for (int a = 0; a < 3; ++a) {
+        if (general) {
+          L.box[6 * i + a] = (cc[a] / 2) * L.d;
+          L.box[6 * i + 3 + a] = std::min((cc[a] / 2 + 1) * L.d, N[a]) - 1;
+        } else {
+          code_extent(N[a], seps[a], cc[a], L.box[6 * i + a], L.box[6 * i + 3 + a]);
+        }
+      }
       bool el = false;
       if (!c.in && t >= std::max(1, op->compress_from_level)) {
         if (op->scheme == SGF_SCHEME_NEST_ALL_ALL) el = cd >= 1;
         else if (op->scheme == SGF_SCHEME_NEST_2_ALL) el = cd == dim - 1;
+        else if (op->scheme == SGF_SCHEME_GEN_ALL_ALL) el = true;
       }
       L.eligible[i] = el;
     }

@@ -160,6 +160,14 @@ def config(name: str, seed: int = 0) -> dict:
         return dict(name=name, dim=3, n=(e, e, e), stencil=STENCIL_7PT_FV_3D,
                     dirichlet=FACE_XM, coeffs=lognormal_field(shape, 8.0, 2.0, seed),
                     leaf=8, degree=2, basis="poly", dof=1)
+    if name.startswith("gengrf3d_"):
+        # the GRF workload on general partitions (Gen-All-All, Sec. 5.2), with
+        # the paper's leaf size for piecewise-quadratic compression (b = 5)
+        e = int(name.split("_")[1])
+        shape = (e, e, e)
+        return dict(name=name, dim=3, n=(e, e, e), stencil=STENCIL_7PT_FV_3D,
+                    dirichlet=FACE_XM, coeffs=lognormal_field(shape, 8.0, 2.0, seed),
+                    leaf=5, degree=2, basis="poly", dof=1, scheme="gen_all_all")
     if name.startswith("twophase3d_"):
         e = int(name.split("_")[1])
         shape = (e, e, e)

@@ -39,15 +39,23 @@ CASES = [
     ((64, 64, 64), 3, 8, "7pt_fv_3d"),
     ((7, 7, 7), 3, 8, "7pt_3d"),
     ((12, 13, 13), 3, 4, "q1_elastic_3d"),
+    ((20, 20, 20), 3, 5, "gen"),
+    ((24, 23, 17), 3, 5, "gen"),
+    ((23, 19, 1), 2, 4, "gen"),
 ]
 
 
 @pytest.mark.parametrize("n,dim,b,st", CASES)
 def test_symbolic_analysis_bit_exact(n, dim, b, st):
     elastic = st == "q1_elastic_3d"
-    H = build_hierarchy(n, dim, b, st, dof=3 if elastic else 1)
+    general = st == "gen"   # general partitions (Gen-All-All)
+    if general:
+        st = "7pt_fv_3d" if dim == 3 else "5pt_2d"
+    H = build_hierarchy(n, dim, b, st, dof=3 if elastic else 1, general=general)
     if elastic:
         P = sgf.Plan(n, dim, st, 1, b, 1, basis=1, dof=3)
+    elif general:
+        P = sgf.Plan(n, dim, st, 1, b, 2 if dim == 3 else 1, scheme="gen_all_all")
     else:
         P = sgf.Plan(n, dim, st, 1, b, 2 if dim == 3 else 1)
     assert P.nlevels == len(H.levels)
@@ -66,9 +74,11 @@ def test_symbolic_analysis_bit_exact(n, dim, b, st):
         if li > 0:
             kids = [ex["child_idx"][ex["child_ptr"][i]:ex["child_ptr"][i + 1]].tolist() for i in range(lev.nnodes)]
             assert kids == lev.children
-        # Nest-All-All eligibility: separators of dimension >= 1
+        # Nest-All-All eligibility: separators of dimension >= 1; Gen-All-All: every node
         want = (~lev.interior) & (lev.cell_dim >= 1)
         assert ex["eligible"].tolist() == want.tolist()
+        if general:
+            assert not lev.interior.any()
 
 
 def test_analyze_rejects_bad_arguments():

@@ -58,6 +58,9 @@ CASES = [
     [[130, 67, 1], 2, "5pt_2d", 15, 8, 2, "mixed", "nest_all_all"],
     [[12, 13, 13], 3, "q1_elastic_3d", 1, 4, 1, "fp64", "nest_all_all"],
     [[24, 25, 25], 3, "q1_elastic_3d", 1, 8, 1, "mixed", "nest_all_all"],
+    [[20, 20, 20], 3, "7pt_fv_3d", 1, 5, 2, "fp64", "gen_all_all"],
+    [[24, 23, 17], 3, "7pt_fv_3d", 1, 5, 2, "mixed", "gen_all_all"],
+    [[23, 19, 1], 2, "5pt_2d", 15, 4, 1, "fp64", "gen_all_all"],
     [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "mixed", "nest_all_all",
      {"gemv_min_elems": 256, "gemv_max_elems": 1024, "front_small": 64, "tensor_cores": 0}],
     [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "fp64", "nest_all_all",

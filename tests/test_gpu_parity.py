@@ -55,11 +55,13 @@ def _problem(name, seed=0):
     return si.config(name, seed)
 
 
-def _oracle(cfg, scheme="nest_all_all"):
+def _oracle(cfg, scheme=None):
+    scheme = scheme or cfg.get("scheme", "nest_all_all")
     key = (cfg["name"], scheme)
     if key not in _ORACLE_CACHE:
         A = assemble(cfg)
-        H = build_hierarchy(cfg["n"], cfg["dim"], cfg["leaf"], cfg["stencil"], dof=cfg.get("dof", 1))
+        H = build_hierarchy(cfg["n"], cfg["dim"], cfg["leaf"], cfg["stencil"], dof=cfg.get("dof", 1),
+                            general=scheme == "gen_all_all")
         F = factorize(A, H, Options(scheme=scheme, degree=cfg["degree"], order="level",
                                     basis=cfg.get("basis", "poly")))
         _ORACLE_CACHE[key] = (A, H, F)
@@ -72,15 +74,16 @@ def _tolerance(cfg, v):
     a, m = O.solve(v), O.multiply(v)
     sa = sm = 0.0
     for seed in range(3):
-        P = factorize(A, H, Options(degree=cfg["degree"], order="level", qr_noise=4 * 2.2e-16,
-                                    qr_noise_seed=seed, basis=cfg.get("basis", "poly")))
+        P = factorize(A, H, Options(scheme=cfg.get("scheme", "nest_all_all"), degree=cfg["degree"],
+                                    order="level", qr_noise=4 * 2.2e-16, qr_noise_seed=seed,
+                                    basis=cfg.get("basis", "poly")))
         sa = max(sa, np.linalg.norm(P.solve(v) - a) / np.linalg.norm(a))
         sm = max(sm, np.linalg.norm(P.multiply(v) - m) / np.linalg.norm(m))
     return max(1e-10, 4 * sa), max(1e-10, 4 * sm)
 
 
-def _gpu(cfg, precision="fp64", scheme="nest_all_all"):
-    plan = sgf.Plan.from_config(cfg, precision=precision, scheme=scheme)
+def _gpu(cfg, precision="fp64", scheme=None):
+    plan = sgf.Plan.from_config(cfg, precision=precision, scheme=scheme or cfg.get("scheme", "nest_all_all"))
     c = torch.tensor(np.ascontiguousarray(cfg["coeffs"]).ravel(), dtype=torch.float64, device=DEV)
     return plan, sgf.Factor(plan, c)
 
@@ -90,7 +93,7 @@ def _t(x):
 
 
 SMALL = ["poisson2d_64", "rand2d_29_23_4", "grf3d_16", "rand3d_21_18_13_4", "grf3d_24",
-         "twophase3d_24", "grf3d_32", "elastic_8", "elastic_12"]
+         "twophase3d_24", "grf3d_32", "elastic_8", "elastic_12", "gengrf3d_20", "gengrf3d_24"]
 
 
 @pytest.mark.parametrize("name", SMALL)
