@@ -1,0 +1,74 @@
+"""Size sweep of the solver on one GPU: 3D Poisson (7-point stencil, unit
+coefficients, Dirichlet on every face) on e^3 grids, Nest-All-All with
+piecewise quadratics, factor + PCG to a relative residual of 1e-10.
+
+The paper's stated aim for its experiments is solve times that scale like
+O(n) with near-flat iteration counts as the grid grows (Sec. 7, up to 16M
+unknowns for Poisson).  This prints, per size, the factor and PCG times, the
+iterations, the apply time, the factor's device memory and the time per
+unknown.
+
+    python -m paper_1907_03406_gb300.sweep --sizes 32 64 128 192 256 --precision mixed
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000):
+    import torch
+
+    import sgf_inputs as si
+
+    from . import Factor, Plan
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rows = []
+    for e in sizes:
+        cfg = si.config(f"poisson3d_{e}")
+        plan = Plan.from_config(cfg, precision=precision)
+        coeffs = torch.tensor(np.ascontiguousarray(cfg["coeffs"]).ravel(), dtype=torch.float64, device=dev)
+        b = torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        F = Factor(plan, coeffs)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        free1 = torch.cuda.mem_get_info()[0]
+        x, info = F.pcg(b, rtol=rtol, maxit=maxit, check=False)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            F.apply(b)
+        e1.record()
+        torch.cuda.synchronize()
+        row = dict(edge=e, n=plan.n, precision=F.precision, factor_ms=round(1e3 * (t1 - t0), 1),
+                   pcg_ms=round(1e3 * (t2 - t1), 1), iterations=info["iterations"],
+                   rel_residual=info["rel_residual"], apply_ms=round(e0.elapsed_time(e1) / 3, 3),
+                   factor_gb=round((free0 - free1) / 1e9, 2),
+                   ns_per_unknown=round(1e9 * (t2 - t0) / plan.n, 1))
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+        F.close()
+        del F, x, coeffs, b
+        torch.cuda.empty_cache()
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--sizes", type=int, nargs="+", default=[32, 64, 128])
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    args = ap.parse_args()
+    run(args.sizes, args.precision)
+
+
+if __name__ == "__main__":
+    main()
