@@ -1636,67 +1636,9 @@ std::unique_ptr<FactorBase> make_factor(const Plan& plan, const double* coeffs, 
 }
 
 // ---------------------------------------------------------------------------
-// PCG (Sec. 7), FP64 vectors; flexible beta with a single-precision factor
+// PCG (Sec. 7), FP64 vectors; flexible beta with a single-precision factor;
+// up to 8 independent recurrences advanced together (one apply per iteration)
 // ---------------------------------------------------------------------------
-int pcg_solve(FactorBase& F, const double* b, double* x, double rtol, int maxit, cudaStream_t s,
-              int* iters, double* relres) {
-  const int64_t n = F.n;
-  double* buf = nullptr;
-  SGF_CK(cudaMallocAsync((void**)&buf, sizeof(double) * (5 * n + kDotBlocks + 8), s));
-  double *r = buf, *z = r + n, *p = z + n, *q = p + n, *ro = q + n, *part = ro + n, *sc = part + kDotBlocks;
-  auto dot = [&](const double* a, const double* c) {
-    launch_dot(a, c, n, part, sc, s);
-    double h;
-    SGF_CK(cudaMemcpyAsync(&h, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
-    SGF_CK(cudaStreamSynchronize(s));
-    return h;
-  };
-  const bool flex = F.mixed();
-  SGF_CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
-  SGF_CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  const double bnorm = std::sqrt(dot(b, b));
-  int it = 0;
-  int rc = SGF_OK;
-  if (bnorm == 0.0) {
-    *iters = 0;
-    *relres = 0.0;
-    SGF_CK(cudaFreeAsync(buf, s));
-    return SGF_OK;
-  }
-  F.apply(r, z, s);
-  SGF_CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  double rz = dot(r, z);
-  while (true) {
-    if (it >= maxit) { rc = SGF_ERR_NO_CONVERGENCE; break; }
-    F.spmv(p, q, s);
-    const double pq = dot(p, q);
-    const double alpha = rz / pq;
-    if (!std::isfinite(alpha)) { rc = SGF_ERR_NONFINITE; break; }
-    launch_axpy(alpha, p, x, n, s);
-    if (flex) SGF_CK(cudaMemcpyAsync(ro, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    launch_axpy(-alpha, q, r, n, s);
-    ++it;
-    const double rr = dot(r, r);
-    if (std::sqrt(rr) <= rtol * bnorm) break;
-    F.apply(r, z, s);
-    const double rz_new = dot(r, z);
-    double beta;
-    if (flex) beta = (rz_new - dot(z, ro)) / rz;
-    else beta = rz_new / rz;
-    rz = rz_new;
-    launch_xpay(z, beta, p, n, s);
-  }
-  // true residual
-  F.spmv(x, q, s);
-  SGF_CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  launch_axpy(-1.0, q, r, n, s);
-  const double tr = std::sqrt(dot(r, r));
-  *iters = it;
-  *relres = tr / bnorm;
-  SGF_CK(cudaFreeAsync(buf, s));
-  return rc;
-}
-
 int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double rtol, int maxit,
                     cudaStream_t s, int* iters, double* relres) {
   const int64_t n = F.n;

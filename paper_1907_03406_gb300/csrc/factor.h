@@ -90,9 +90,6 @@ class FactorBase {
 
 std::unique_ptr<FactorBase> make_factor(const Plan& plan, const double* coeffs_dev, cudaStream_t s);
 
-// PCG (Sec. 7) on an existing factor; returns SGF_OK or SGF_ERR_NO_CONVERGENCE
-int pcg_solve(FactorBase& F, const double* b, double* x, double rtol, int maxit, cudaStream_t s,
-              int* iters, double* relres);
 // nrhs (<= 8) independent PCG recurrences advanced together (one apply per
 // iteration for all of them); iters/relres per RHS
 int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double rtol, int maxit,
