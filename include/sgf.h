@@ -259,13 +259,15 @@ const char* sgf_last_error(void);
 int64_t sgf_dry_run_violations(int reset);
 const char* sgf_dry_run_report(void);
 
-/* Launch accounting for benchmarks.  Kernel kinds 0..10 are named by
+/* Launch accounting for benchmarks.  Kinds 0..11 are named by
  * sgf_profile_kind_name (k_gemm, k_diag, k_copy, k_qrcp, k_gemv_n, k_gemv_t,
- * k_veccopy, k_assemble, k_spmv, k_dot, k_vector).  sgf_profile_reset clears
+ * k_veccopy, k_assemble, k_spmv, k_dot, k_vector, apply); "apply" is one
+ * replay of the graph that applies A_l^{-1} (Sec. 4.7), whose kernels are
+ * also counted, untimed, under their own kinds.  sgf_profile_reset clears
  * the counters; with timing = 1 every later launch is bracketed by CUDA
  * events on its own stream, with timing = 2 only the factor's contraction
- * launches (k_gemm, k_diag, k_qrcp: far fewer, so the events barely perturb a
- * timed step), with 0 none.  sgf_profile_read (synchronizes on the recorded
+ * launches (k_gemm, k_diag, k_qrcp) and the apply replays (far fewer, so the
+ * events barely perturb a timed step), with 0 none.  sgf_profile_read (synchronizes on the recorded
  * events) returns, for one kind, the launches since the reset, their summed
  * device time in ms (0 without timing) and the algorithmic flops and bytes
  * the host attached to them.  Not thread-safe with concurrent factors.      */

@@ -239,7 +239,7 @@ def solve_host(plan: Plan, coeffs: np.ndarray, b: np.ndarray, rtol=1e-10, maxit=
 def profile_reset(timing=False):
     """Clear the launch counters.  timing: False (none), True or "all" (every
     launch bracketed by CUDA events), "contractions" (only the factor's GEMM,
-    front and QR launches)."""
+    front and QR launches and the apply graph replays)."""
     mode = {False: 0, True: 1, "all": 1, "contractions": 2}[timing]
     L.load().sgf_profile_reset(mode)
 

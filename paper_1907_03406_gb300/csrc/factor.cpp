@@ -778,8 +778,17 @@ class FactorImpl final : public FactorBase {
       for (auto& op : P.ops) op(P.b.dev, s);
     } else {
       if (!P.exec) capture(P);
-      SGF_CK(cudaGraphLaunch(P.exec, s));
-      for (const auto& a : P.acct) prof_count(a.kind, a.flops, a.bytes);
+      {
+        double fl = 0, by = 0;
+        for (const auto& a : P.acct) {
+          prof_count(a.kind, a.flops, a.bytes);
+          fl += a.flops;
+          by += a.bytes;
+        }
+        prof_work(fl, by);
+        ProfScope ps(P_APPLY, s);
+        SGF_CK(cudaGraphLaunch(P.exec, s));
+      }
     }
     launch_scatter<T>(v1, perm1_, y, n, nrhs, nr, s);
   }
@@ -791,7 +800,13 @@ class FactorImpl final : public FactorBase {
     prof_capture(true);
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      for (auto& op : P.ops) op(P.b.dev, cs);
+      // every kernel after the first may launch programmatically (its
+      // prologue overlaps the previous kernel's tail)
+      for (size_t i = 0; i < P.ops.size(); ++i) {
+        set_dependent_launch(i > 0);
+        P.ops[i](P.b.dev, cs);
+      }
+      set_dependent_launch(false);
       e = cudaStreamEndCapture(cs, &P.graph);
     }
     prof_capture(false);

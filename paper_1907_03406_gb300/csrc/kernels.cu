@@ -1064,6 +1064,14 @@ __device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
 }
 
+// Programmatic dependent launch: every block of an apply kernel lets the next
+// kernel of the program launch as soon as it has started (once all blocks
+// have, the next grid may fill the SMs this one frees), and waits for the
+// previous grid's completion and memory flush before it touches a vector.
+// Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // One column of an op N step: its x entries (scaled) and the band rows of the
 // current pass (zero outside the band and, for a lower-triangular block,
 // above the diagonal).
@@ -1104,6 +1112,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restri
   constexpr int MP = MT / NR > 0 ? MT / NR : 1;   // 32-row groups per pass
   // two columns per step unless that would cost too many registers (FP64, wide bands)
   constexpr bool kTwo = sizeof(T) == 4 || MP <= 8;
+  pdl_trigger();
   const GemvTask<T> tk = tasks[blockIdx.x];
   __shared__ GemvStage<T> S;
   __shared__ T red[kWarps][32 * MP * NR];
@@ -1119,6 +1128,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restri
       l2_prefetch(cb.A + (size_t)j * cb.lda + rs, sizeof(T) * (size_t)(tk.M - rs));
     }
   }
+  pdl_wait();   // x, y and the partials are written by earlier kernels
   for (int r0 = 0; r0 < tk.M; r0 += 32 * MP) {
     T acc[MP][NR];
 #pragma unroll
@@ -1180,6 +1190,7 @@ __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
                                                      const GemvContrib<T>* __restrict__ cons) {
   constexpr int kWarps = kThreads / 32;
   constexpr int CW = kGemvCols / kWarps;
+  pdl_trigger();
   const GemvTask<T> tk = tasks[blockIdx.x];
   __shared__ GemvStage<T> S;
   gemv_stage(tk, cons, true, S);
@@ -1196,6 +1207,7 @@ __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
     if (cb.tri && cb.upper) i1 = min(i1, cb.tri + o);   // rows <= tri - 1 + o
     if (i1 > i0) l2_prefetch(cb.A + (size_t)o * cb.lda + i0, sizeof(T) * (size_t)(i1 - i0));
   }
+  pdl_wait();   // x, y and the partials are written by earlier kernels
   T acc[CW][NR];
 #pragma unroll
   for (int u = 0; u < CW; ++u)
@@ -1253,6 +1265,8 @@ __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_vgather(const T* __restrict__ src, const int* __restrict__ idx,
                                                       T* __restrict__ dst, int n, int nr) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= (int64_t)n * nr) return;
   const int64_t p = e / nr, q = e - p * nr;
@@ -1262,7 +1276,9 @@ __global__ void __launch_bounds__(kThreads) k_vgather(const T* __restrict__ src,
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_veccopy(const VecCopyTask* __restrict__ tasks,
                                                       const T* __restrict__ src, T* __restrict__ dst) {
+  pdl_trigger();
   const VecCopyTask tk = tasks[blockIdx.x];
+  pdl_wait();
   for (int i = threadIdx.x; i < tk.len; i += kThreads) dst[tk.dst + i] = src[tk.src + i];
 }
 
@@ -1680,10 +1696,46 @@ static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int
   }
 }
 
+namespace {
+thread_local bool t_dependent = false;
+
+// <<<grid, kThreads>>> launch, with the programmatic-serialization attribute
+// while dependent launch is on for this thread
+template <typename... KArgs, typename... Args>
+void launch_apply_kernel(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+  if (!t_dependent) {
+    kern<<<grid, kThreads, 0, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  // a failed launch is reported like a <<<>>> launch: by the caller's
+  // cudaGetLastError, or by the end of the stream capture it belongs to
+  (void)cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+}  // namespace
+
+bool dependent_launch_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("SGF_DEPENDENT_LAUNCH");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+void set_dependent_launch(bool on) { t_dependent = on && dependent_launch_enabled(); }
+
 template <typename T, int NR>
 static void gemv_n_mt(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int max_m, cudaStream_t s) {
-  if (max_m <= 256) k_gemv_n<T, NR, 8><<<n, kThreads, 0, s>>>(tasks, cons);
-  else k_gemv_n<T, NR, 16><<<n, kThreads, 0, s>>>(tasks, cons);
+  if (max_m <= 256) launch_apply_kernel(k_gemv_n<T, NR, 8>, n, s, tasks, cons);
+  else launch_apply_kernel(k_gemv_n<T, NR, 16>, n, s, tasks, cons);
 }
 
 template <typename T>
@@ -1706,10 +1758,10 @@ void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, 
   if (n <= 0) return;
   ProfScope ps(P_GEMV_T, s);
   switch (nr) {
-    case 1: k_gemv_t<T, 1><<<n, kThreads, 0, s>>>(tasks, cons); break;
-    case 2: k_gemv_t<T, 2><<<n, kThreads, 0, s>>>(tasks, cons); break;
-    case 4: k_gemv_t<T, 4><<<n, kThreads, 0, s>>>(tasks, cons); break;
-    default: k_gemv_t<T, 8><<<n, kThreads, 0, s>>>(tasks, cons); break;
+    case 1: launch_apply_kernel(k_gemv_t<T, 1>, n, s, tasks, cons); break;
+    case 2: launch_apply_kernel(k_gemv_t<T, 2>, n, s, tasks, cons); break;
+    case 4: launch_apply_kernel(k_gemv_t<T, 4>, n, s, tasks, cons); break;
+    default: launch_apply_kernel(k_gemv_t<T, 8>, n, s, tasks, cons); break;
   }
 }
 
@@ -1724,7 +1776,7 @@ void launch_vgather(const T* src, const int* idx, T* dst, int n, int nr, cudaStr
   if (n <= 0) return;
   ProfScope ps(P_VECCOPY, s);
   const int64_t tot = (int64_t)n * nr;
-  k_vgather<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(src, idx, dst, n, nr);
+  launch_apply_kernel(k_vgather<T>, (unsigned)((tot + kThreads - 1) / kThreads), s, src, idx, dst, n, nr);
 }
 
 template <typename T>
@@ -1738,7 +1790,7 @@ void launch_veccopy(const VecCopyTask* tasks, int n, const T* src, T* dst, cudaS
   }
   if (n <= 0) return;
   ProfScope ps(P_VECCOPY, s);
-  k_veccopy<T><<<n, kThreads, 0, s>>>(tasks, src, dst);
+  launch_apply_kernel(k_veccopy<T>, (unsigned)n, s, tasks, src, dst);
 }
 
 template <typename T>

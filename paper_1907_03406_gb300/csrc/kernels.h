@@ -25,6 +25,15 @@ void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* cont
                     cudaStream_t s);
 // tensor-core GEMMs for the FP32 factor unless SGF_TENSOR_CORES=0
 bool gemm_tc_enabled();
+// Programmatic dependent launch of the apply kernels (k_gemv_n, k_gemv_t,
+// k_vgather, k_veccopy) on this thread, set while an apply program is
+// captured into a graph: each such launch may start while the previous
+// kernel drains; its blocks stage their task lists and prefetch their matrix
+// columns into L2 (data no earlier kernel of the program writes), then wait
+// for the previous grid's completion before reading vectors or writing
+// results.  Off when SGF_DEPENDENT_LAUNCH=0.
+void set_dependent_launch(bool on);
+bool dependent_launch_enabled();
 template <typename T>
 void launch_diag(const DiagTask<T>* tasks, int ntasks, DevStatus* st, int level, cudaStream_t s);
 // whole blocked Cholesky + inverse of small fronts, one CTA each

@@ -69,7 +69,7 @@ ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
   a.flops += S.next_flops;
   a.bytes += S.next_bytes;
   S.next_flops = S.next_bytes = 0;
-  const bool timed = S.timing == 1 || (S.timing == 2 && (kind == P_GEMM || kind == P_DIAG || kind == P_QR));
+  const bool timed = S.timing == 1 || (S.timing == 2 && (kind == P_GEMM || kind == P_DIAG || kind == P_QR || kind == P_APPLY));
   if (timed) {
     Pending p;
     p.a = get_event(S);
@@ -122,7 +122,7 @@ int prof_read(int kind, long long* launches, double* ms, double* flops, double* 
 
 const char* prof_name(int kind) {
   static const char* n[P_NKINDS] = {"k_gemm",   "k_diag",     "k_copy", "k_qrcp", "k_gemv_n", "k_gemv_t",
-                                    "k_veccopy", "k_assemble", "k_spmv", "k_dot",  "k_vector"};
+                                    "k_veccopy", "k_assemble", "k_spmv", "k_dot",  "k_vector", "apply"};
   return (kind >= 0 && kind < P_NKINDS) ? n[kind] : "?";
 }
 

@@ -10,7 +10,9 @@ namespace sgf {
 
 enum ProfKind {
   P_GEMM = 0, P_DIAG, P_COPY, P_QR, P_GEMV_N, P_GEMV_T, P_VECCOPY, P_ASSEMBLE, P_SPMV, P_DOT,
-  P_VEC, P_NKINDS
+  P_VEC,
+  P_APPLY,   // one replay of an apply program's graph (its kernels are counted under their own kinds)
+  P_NKINDS
 };
 
 // work of the next launch (set by the code that built its tasks)
@@ -33,6 +35,7 @@ void prof_count(int kind, double flops, double bytes);
 void prof_capture(bool on);
 
 // timing: 0 none, 1 every launch, 2 the factor contractions (GEMM, fronts, QR)
+// and the apply graph replays
 void prof_reset(int timing);
 int prof_read(int kind, long long* launches, double* ms, double* flops, double* bytes);
 const char* prof_name(int kind);
