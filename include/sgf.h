@@ -259,6 +259,17 @@ const char* sgf_last_error(void);
 int64_t sgf_dry_run_violations(int reset);
 const char* sgf_dry_run_report(void);
 
+/* Device memory.  Factors, their apply programs and solver work buffers are
+ * allocated from the current device's default stream-ordered pool, which
+ * keeps blocks freed by sgf_factor_destroy cached for the next factorization
+ * (no driver allocation or unmapping per factorization).  The cache counts
+ * as used memory for other allocators in the process (e.g. PyTorch's);
+ * sgf_release_cached_memory synchronizes the current device and hands the
+ * unused cached blocks back.  An allocation of this library that fails does
+ * the same once before it reports SGF_ERR_OOM.  Returns SGF_OK or
+ * SGF_ERR_CUDA.                                                           */
+int sgf_release_cached_memory(void);
+
 /* Launch accounting for benchmarks.  Kinds 0..11 are named by
  * sgf_profile_kind_name (k_gemm, k_diag, k_copy, k_qrcp, k_gemv_n, k_gemv_t,
  * k_veccopy, k_assemble, k_spmv, k_dot, k_vector, apply); "apply" is one

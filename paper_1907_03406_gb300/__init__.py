@@ -244,6 +244,12 @@ def profile_reset(timing=False):
     L.load().sgf_profile_reset(mode)
 
 
+def release_cached_memory():
+    """Hand the device memory cached by freed factors back to the device
+    (synchronizes the current device)."""
+    _check(L.load().sgf_release_cached_memory(), "release_cached_memory")
+
+
 def profile_read() -> dict:
     """{kernel name: dict(launches, ms, flops, bytes)} since the last reset."""
     lib = L.load()

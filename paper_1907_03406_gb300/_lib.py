@@ -66,6 +66,7 @@ SIGNATURES = {
     "sgf_profile_reset": (None, [_I]),
     "sgf_profile_read": (_I, [_I, _I64P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sgf_profile_kind_name": (C.c_char_p, [_I]),
+    "sgf_release_cached_memory": (_I, []),
 }
 
 _lib = None

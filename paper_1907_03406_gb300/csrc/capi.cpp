@@ -364,4 +364,10 @@ int sgf_profile_read(int kind, int64_t* launches, double* ms, double* flops, dou
   return SGF_OK;
 }
 const char* sgf_profile_kind_name(int kind) { return sgf::prof_name(kind); }
+
+int sgf_release_cached_memory(void) {
+  if (!sgf::dry_run() && cudaDeviceSynchronize() != cudaSuccess) return SGF_ERR_CUDA;
+  sgf::dev_release_cached();
+  return SGF_OK;
+}
 }

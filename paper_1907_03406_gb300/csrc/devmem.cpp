@@ -85,8 +85,24 @@ void* dev_malloc_async(size_t bytes, cudaStream_t s) {
     }
   }
   void* p = nullptr;
-  SGF_CK(cudaMallocAsync(&p, bytes, s));
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e == cudaErrorMemoryAllocation) {
+    // the pool may be holding freed blocks of earlier factorizations: hand
+    // them back to the device and try once more
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    dev_release_cached();
+    e = cudaMallocAsync(&p, bytes, s);
+  }
+  SGF_CK(e);
   return p;
+}
+void dev_release_cached() {
+  if (dry_run()) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
 }
 void dev_free_async(void* p, cudaStream_t s) {
   if (dry_run()) return fake_free(p);

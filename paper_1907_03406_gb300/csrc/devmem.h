@@ -19,8 +19,13 @@ bool dry_run();
 
 void* dev_malloc(size_t bytes);                          // persistent (cudaMalloc)
 void dev_free(void* p);
-void* dev_malloc_async(size_t bytes, cudaStream_t s);    // stream ordered
+// stream ordered, from the device's default pool, which keeps freed blocks
+// cached for later allocations (an allocation that fails hands the cached
+// blocks back and retries once)
+void* dev_malloc_async(size_t bytes, cudaStream_t s);
 void dev_free_async(void* p, cudaStream_t s);
+// return the pool's unused cached blocks to the device
+void dev_release_cached();
 void dev_memset(void* p, int v, size_t bytes, cudaStream_t s);
 void dev_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
 void dev_d2h(void* dst, const void* src, size_t bytes, cudaStream_t s);  // synchronous

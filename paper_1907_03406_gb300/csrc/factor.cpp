@@ -61,6 +61,20 @@ std::vector<std::vector<char>>& host_pool() {
   thread_local std::vector<std::vector<char>> p;
   return p;
 }
+// keep at most 16 buffers, the largest ones
+void host_pool_put(std::vector<char>&& v) {
+  if (v.capacity() == 0) return;
+  v.clear();
+  auto& p = host_pool();
+  if (p.size() < 16) {
+    p.push_back(std::move(v));
+    return;
+  }
+  size_t k = 0;
+  for (size_t i = 1; i < p.size(); ++i)
+    if (p[i].capacity() < p[k].capacity()) k = i;
+  if (p[k].capacity() < v.capacity()) p[k] = std::move(v);
+}
 struct PinnedPool {
   std::vector<std::pair<char*, size_t>> bufs;
   ~PinnedPool() {
@@ -111,18 +125,27 @@ void Batch::run(cudaStream_t s) {
 }
 
 
-Batch::Batch() {
+Batch::Batch() {}
+
+void Batch::grow(size_t want) {
   auto& p = host_pool();
-  if (!p.empty()) {
-    host.swap(p.back());
-    p.pop_back();
-    host.clear();
+  int best = -1;   // the smallest pooled buffer that is large enough
+  for (int i = 0; i < (int)p.size(); ++i)
+    if (p[i].capacity() >= want && (best < 0 || p[i].capacity() < p[best].capacity())) best = i;
+  std::vector<char> v;
+  if (best >= 0) {
+    v.swap(p[best]);
+    p.erase(p.begin() + best);
+  } else {
+    v.reserve(want);
   }
+  v.assign(host.begin(), host.end());
+  host.swap(v);
+  host_pool_put(std::move(v));
 }
 
 Batch::~Batch() {
-  host.clear();
-  if (host_pool().size() < 8) host_pool().push_back(std::move(host));
+  host_pool_put(std::move(host));
   for (int i = 0; i < kRing; ++i) {
     if (ev[i]) {
       cudaEventSynchronize(ev[i]);
@@ -143,7 +166,7 @@ void Batch::upload_persistent(cudaStream_t s) {
     dev = keep_host.data();
     return;
   }
-  dev = (char*)dev_malloc(host.size());
+  dev = (char*)dev_malloc_async(host.size(), s);
   cap = host.size();
   dev_h2d(dev, host.data(), host.size(), s);
   dev_sync(s);
@@ -435,7 +458,7 @@ void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, Dev
 template <typename T>
 T* dalloc(std::vector<void*>& keep, size_t count, cudaStream_t s, bool zero = true) {
   if (count == 0) count = 1;
-  T* p = (T*)dev_malloc(count * sizeof(T));
+  T* p = (T*)dev_malloc_async(count * sizeof(T), s);
   keep.push_back(p);
   if (zero) dev_memset(p, 0, count * sizeof(T), s);
   return p;
@@ -476,13 +499,32 @@ struct LevelRec {
 // a fixed sequence of batched launches (replayed as one CUDA graph)
 template <typename T>
 struct Program {
-  Batch b;
-  std::vector<std::function<void(const char*, cudaStream_t)>> ops;
+  using Op = std::function<void(const char*, cudaStream_t)>;
   struct Acct { int kind; double flops, bytes; };
+  Batch b;
+  std::vector<Op> ops;
   std::vector<Acct> acct;      // launch accounting added per replay
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   std::vector<void*> mem;      // split-GEMV partial sums and counters
+  // launches of one part of the program, recorded before the parts are put
+  // in apply order (they share the program's staging batch and memory)
+  struct Piece {
+    std::vector<Op> ops;
+    std::vector<Acct> acct;
+  };
+  std::vector<Piece> down, up;   // per level: the part before / after the top
+  int levels_built = 0;
+};
+
+// where GemvList::emit and friends record: a program's batch and memory with
+// the launch list of one of its pieces
+template <typename T>
+struct ProgramSink {
+  Batch& b;
+  std::vector<void*>& mem;
+  std::vector<typename Program<T>::Op>& ops;
+  std::vector<typename Program<T>::Acct>& acct;
 };
 
 // Element budget of one GEMV task (one CTA): the launch's elements spread
@@ -641,8 +683,8 @@ struct GemvList {
     T* part = nullptr;
     int* cnt = nullptr;
     if (ncnt > 0) {
-      part = (T*)dev_malloc(npart * sizeof(T));
-      cnt = (int*)dev_malloc((size_t)ncnt * sizeof(int));
+      part = (T*)dev_malloc_async(npart * sizeof(T), s);
+      cnt = (int*)dev_malloc_async((size_t)ncnt * sizeof(int), s);
       dev_memset(cnt, 0, (size_t)ncnt * sizeof(int), s);
       P.mem.push_back(part);
       P.mem.push_back(cnt);
@@ -690,7 +732,7 @@ class FactorImpl final : public FactorBase {
     plan = &P;
     n = P.n;
     tune_ = P.tune;   // a factor keeps the launch shapes it was made with
-    st_ = (DevStatus*)dev_malloc(sizeof(DevStatus));
+    st_ = (DevStatus*)dev_malloc_async(sizeof(DevStatus), s);
     dev_memset(st_, 0, sizeof(DevStatus), s);
     try {
       build(coeffs, s);
@@ -737,20 +779,24 @@ class FactorImpl final : public FactorBase {
   sgf_tuning tune_{};
   std::mutex prog_mu_;
 
+  // Everything the factor holds came from the stream-ordered pool; after the
+  // device is idle it goes back to the pool (no unmapping, so the next
+  // factorization of a plan of this size allocates without driver calls).
   void release() {
     if (!dry_run()) cudaDeviceSynchronize();
-    for (void* p : keep_) dev_free(p);
+    cudaStream_t s0 = nullptr;
+    for (void* p : keep_) dev_free_async(p, s0);
     keep_.clear();
-    if (st_) dev_free(st_);
+    if (st_) dev_free_async(st_, s0);
     st_ = nullptr;
     for (int k = 0; k < 4; ++k)
       for (Program<T>* P : {&inv_[k], &fwd_[k]}) {
         if (!dry_run()) {
-          if (P->b.dev) dev_free(P->b.dev);
+          if (P->b.dev) dev_free_async(P->b.dev, s0);
           if (P->exec) cudaGraphExecDestroy(P->exec);
           if (P->graph) cudaGraphDestroy(P->graph);
         }
-        for (void* m : P->mem) dev_free(m);
+        for (void* m : P->mem) dev_free_async(m, s0);
         P->mem.clear();
         P->b.dev = nullptr;
         P->exec = nullptr;
@@ -1195,6 +1241,12 @@ class FactorImpl final : public FactorBase {
         b.run(s);
       }
       trace(s, lvl, "compression issued");
+      // the level below is complete: record its parts of the apply program
+      // while the GPU works through this level (the host waits next)
+      if (li >= 1) {
+        prebuild_level((int)li - 1, lay.vec_size, s);
+        trace(s, lvl, "apply parts, level below");
+      }
       check_status(s);
       trace(s, lvl, "compression to QR");
       std::vector<int> rk(ne, 0);
@@ -1395,11 +1447,23 @@ class FactorImpl final : public FactorBase {
   // apply programs
   // ----------------------------------------------------------------------
   static constexpr int kMaxNr = 8;
+  // level-vector buffers [v | w | kept] of non-top level t
+  void ensure_vb(int t, int64_t vec_size, cudaStream_t s) {
+    if ((int)vb_.size() > t) return;
+    vb_.resize(t + 1, nullptr);
+    vb_[t] = dalloc<T>(keep_, 3 * (size_t)kMaxNr * std::max<int64_t>(vec_size, 1), s);
+  }
+  // While the GPU factors level t + 1 (vec_size: its vector length), the host
+  // records the single-RHS inverse program's parts for the finished level t.
+  void prebuild_level(int t, int64_t next_vec_size, cudaStream_t s) {
+    ensure_vb(t, lev_[t].lay.vec_size, s);
+    ensure_vb(t + 1, next_vec_size, s);
+    TuneScope tscope(&tune_);
+    inverse_level(inv_[0], t, 1, s);
+  }
   void build_programs(cudaStream_t s) {
     const int nl = (int)lev_.size();
-    vb_.resize(nl);
-    for (int t = 0; t < nl; ++t)
-      vb_[t] = dalloc<T>(keep_, 3 * (size_t)kMaxNr * std::max<int64_t>(lev_[t].lay.vec_size, 1), s);
+    for (int t = (int)vb_.size(); t < nl; ++t) ensure_vb(t, lev_[t].lay.vec_size, s);
     vtop_ = dalloc<T>(keep_, 2 * (size_t)kMaxNr * std::max(mtop_, 1), s);
     program(true, 1, s);   // the forward (multiply) programs are built on first use
   }
@@ -1416,7 +1480,7 @@ class FactorImpl final : public FactorBase {
     return P;
   }
 
-  T* base(int t) { return t < (int)lev_.size() ? vb_[t] : vtop_; }
+  T* base(int t) { return t < (int)vb_.size() ? vb_[t] : vtop_; }
 
   // interior neighbours of each separator (owner-computes lists)
   std::vector<std::vector<std::pair<int, int>>> sep_interiors(const LevelRec<T>& R, int nnodes) {
@@ -1426,7 +1490,8 @@ class FactorImpl final : public FactorBase {
     return out;
   }
 
-  void veccopy(Program<T>& P, std::vector<VecCopyTask>& v, const T* src, T* dst) {
+  template <class Sink>
+  void veccopy(Sink& P, std::vector<VecCopyTask>& v, const T* src, T* dst) {
     if (!v.empty()) {
       double by = 0;
       for (const auto& t : v) by += 2.0 * sizeof(T) * t.len;
@@ -1437,113 +1502,146 @@ class FactorImpl final : public FactorBase {
     });
   }
 
+  // A_l^{-1} x in apply order: for each level upward the interior solve and
+  // separator update (down part), the top solve, then for each level
+  // downward the back substitution (up part).  The parts of a level are
+  // recorded as soon as the level is factored; the program is put together
+  // once all are.
+  void inverse_level(Program<T>& P, int t, int nr, cudaStream_t s) {
+    if (t < P.levels_built) return;
+    P.down.resize(t + 1);
+    P.up.resize(t + 1);
+    ProgramSink<T> d{P.b, P.mem, P.down[t].ops, P.down[t].acct};
+    inverse_down(d, t, nr, s);
+    ProgramSink<T> u{P.b, P.mem, P.up[t].ops, P.up[t].acct};
+    inverse_up(u, t, nr, s);
+    P.levels_built = t + 1;
+  }
+
   void build_inverse(Program<T>& P, int nr, cudaStream_t s) {
     const int nl = (int)lev_.size();
-    for (int t = 0; t < nl; ++t) {
-      const LevelRec<T>& R = lev_[t];
-      const auto& lay = R.lay;
-      const int64_t vs = lay.vec_size;
-      T* v = base(t);
-      T* w = v + vs * nr;
-      T* kp = v + 2 * vs * nr;
-      // every large product is a column dot product: L^{-1} x through the
-      // mirrored upper triangle, W^T x and L^{-T} x through the columns
-      GemvList<T> f1(nr), f2(nr), f3(nr), f4(nr);
-      f1.trans = f2.trans = f3.trans = f4.trans = true;
-      for (const auto& r : R.in)
-        f1.add(w + nr * lay.vec_off[r.node], r.m, 0,
-               {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1), true}});
-      auto si = sep_interiors(R, (int)lay.m.size());
-      for (int S = 0; S < (int)si.size(); ++S) {
-        if (si[S].empty()) continue;
-        std::vector<typename GemvList<T>::In> ins;
-        for (auto [a, col] : si[S]) {
-          const auto& r = R.in[a];
-          ins.push_back({r.W + (size_t)col * r.m, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
-        }
-        f2.add(v + nr * lay.vec_off[S], lay.m[S], 1, ins);
-      }
-      for (const auto& c : R.sep) {
-        if (!c.comp) continue;
-        f3.add(w + nr * lay.vec_off[c.node], c.m, 0,
-               {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1), true}});
-        f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
-      }
-      f1.emit(P, s);
-      f2.emit(P, s);
-      f3.emit(P, s);
-      f4.emit(P, s);
-      std::vector<VecCopyTask> vc;
-      for (const auto& c : R.sep)
-        if (c.k > 0) vc.push_back({nr * ((c.comp ? 2 * vs : 0) + lay.vec_off[c.node]), nr * c.dst, nr * c.k, 0});
-      veccopy(P, vc, v, base(t + 1));
-    }
-    // top
-    {
-      T* v = vtop_;
-      T* w = vtop_ + (size_t)mtop_ * nr;
-      GemvList<T> a(nr), bt(nr);
-      a.trans = bt.trans = true;
-      a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1), true}});
-      bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
-      a.emit(P, s);
-      bt.emit(P, s);
-    }
-    for (int t = nl - 1; t >= 0; --t) {
-      const LevelRec<T>& R = lev_[t];
-      const auto& lay = R.lay;
-      const int64_t vs = lay.vec_size;
-      T* v = base(t);
-      T* w = v + vs * nr;
-      T* kp = v + 2 * vs * nr;
-      T* vn = base(t + 1);
-      std::vector<VecCopyTask> vc;
-      for (const auto& c : R.sep)
-        if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
-      veccopy(P, vc, vn, v);
-      GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
-      b2.trans = b3.trans = b4.trans = true;
-      for (const auto& c : R.sep) {
-        if (!c.comp) continue;
-        b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
-        b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
-      }
-      // w_I -= W x_S: the separator values of every interior are gathered into
-      // one contiguous vector in W's column order, so each row of W (a column
-      // of W^T) is a single dense dot product
-      std::vector<int> gidx;
-      std::vector<int64_t> goff(R.in.size());
-      for (size_t a = 0; a < R.in.size(); ++a) {
+    for (int t = P.levels_built; t < nl; ++t) inverse_level(P, t, nr, s);
+    auto take = [&P](typename Program<T>::Piece& q) {
+      for (auto& o : q.ops) P.ops.push_back(std::move(o));
+      P.acct.insert(P.acct.end(), q.acct.begin(), q.acct.end());
+      q = {};
+    };
+    for (int t = 0; t < nl; ++t) take(P.down[t]);
+    ProgramSink<T> top{P.b, P.mem, P.ops, P.acct};
+    inverse_top(top, nr, s);
+    for (int t = nl - 1; t >= 0; --t) take(P.up[t]);
+    P.down.clear();
+    P.up.clear();
+  }
+
+  template <class Sink>
+  void inverse_down(Sink& P, int t, int nr, cudaStream_t s) {
+    const LevelRec<T>& R = lev_[t];
+    const auto& lay = R.lay;
+    const int64_t vs = lay.vec_size;
+    T* v = base(t);
+    T* w = v + vs * nr;
+    T* kp = v + 2 * vs * nr;
+    // every large product is a column dot product: L^{-1} x through the
+    // mirrored upper triangle, W^T x and L^{-T} x through the columns
+    GemvList<T> f1(nr), f2(nr), f3(nr), f4(nr);
+    f1.trans = f2.trans = f3.trans = f4.trans = true;
+    for (const auto& r : R.in)
+      f1.add(w + nr * lay.vec_off[r.node], r.m, 0,
+             {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1), true}});
+    auto si = sep_interiors(R, (int)lay.m.size());
+    for (int S = 0; S < (int)si.size(); ++S) {
+      if (si[S].empty()) continue;
+      std::vector<typename GemvList<T>::In> ins;
+      for (auto [a, col] : si[S]) {
         const auto& r = R.in[a];
-        goff[a] = (int64_t)gidx.size();
-        gidx.resize(gidx.size() + r.s);
-        for (auto [S, col] : r.nb)
-          for (int j = 0; j < lay.m[S]; ++j) gidx[goff[a] + col + j] = (int)(lay.vec_off[S] + j);
+        ins.push_back({r.W + (size_t)col * r.m, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
       }
-      T* xs = nullptr;
-      if (!gidx.empty()) {
-        xs = (T*)dev_malloc(sizeof(T) * gidx.size() * nr);
-        P.mem.push_back(xs);
-      }
-      for (size_t a = 0; a < R.in.size(); ++a) {
-        const auto& r = R.in[a];
-        if (r.s > 0) b3.add(w + nr * lay.vec_off[r.node], r.m, 1, {{r.Wt, r.s, xs + nr * goff[a], nullptr, r.s, false, T(-1)}});
-        b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
-      }
-      b1.emit(P, s);
-      b2.emit(P, s);
-      if (!gidx.empty()) {
-        const size_t oi = P.b.push(gidx);
-        const int ng = (int)gidx.size(), r = nr;
-        const T* src = v;
-        P.acct.push_back({P_VECCOPY, 0.0, 2.0 * sizeof(T) * ng * r + 4.0 * ng});
-        P.ops.push_back([=](const char* d, cudaStream_t st) {
-          launch_vgather<T>(src, (const int*)(d + oi), xs, ng, r, st);
-        });
-      }
-      b3.emit(P, s);
-      b4.emit(P, s);
+      f2.add(v + nr * lay.vec_off[S], lay.m[S], 1, ins);
     }
+    for (const auto& c : R.sep) {
+      if (!c.comp) continue;
+      f3.add(w + nr * lay.vec_off[c.node], c.m, 0,
+             {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1), true}});
+      f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
+    }
+    f1.emit(P, s);
+    f2.emit(P, s);
+    f3.emit(P, s);
+    f4.emit(P, s);
+    std::vector<VecCopyTask> vc;
+    for (const auto& c : R.sep)
+      if (c.k > 0) vc.push_back({nr * ((c.comp ? 2 * vs : 0) + lay.vec_off[c.node]), nr * c.dst, nr * c.k, 0});
+    veccopy(P, vc, v, base(t + 1));
+  }
+
+  template <class Sink>
+  void inverse_top(Sink& P, int nr, cudaStream_t s) {
+    T* v = vtop_;
+    T* w = vtop_ + (size_t)mtop_ * nr;
+    GemvList<T> a(nr), bt(nr);
+    a.trans = bt.trans = true;
+    a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1), true}});
+    bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
+    a.emit(P, s);
+    bt.emit(P, s);
+  }
+
+  template <class Sink>
+  void inverse_up(Sink& P, int t, int nr, cudaStream_t s) {
+    const LevelRec<T>& R = lev_[t];
+    const auto& lay = R.lay;
+    const int64_t vs = lay.vec_size;
+    T* v = base(t);
+    T* w = v + vs * nr;
+    T* kp = v + 2 * vs * nr;
+    T* vn = base(t + 1);
+    std::vector<VecCopyTask> vc;
+    for (const auto& c : R.sep)
+      if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
+    veccopy(P, vc, vn, v);
+    GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
+    b2.trans = b3.trans = b4.trans = true;
+    for (const auto& c : R.sep) {
+      if (!c.comp) continue;
+      b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
+      b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+    }
+    // w_I -= W x_S: the separator values of every interior are gathered into
+    // one contiguous vector in W's column order, so each row of W (a column
+    // of W^T) is a single dense dot product
+    std::vector<int> gidx;
+    std::vector<int64_t> goff(R.in.size());
+    for (size_t a = 0; a < R.in.size(); ++a) {
+      const auto& r = R.in[a];
+      goff[a] = (int64_t)gidx.size();
+      gidx.resize(gidx.size() + r.s);
+      for (auto [S, col] : r.nb)
+        for (int j = 0; j < lay.m[S]; ++j) gidx[goff[a] + col + j] = (int)(lay.vec_off[S] + j);
+    }
+    T* xs = nullptr;
+    if (!gidx.empty()) {
+      xs = (T*)dev_malloc_async(sizeof(T) * gidx.size() * nr, s);
+      P.mem.push_back(xs);
+    }
+    for (size_t a = 0; a < R.in.size(); ++a) {
+      const auto& r = R.in[a];
+      if (r.s > 0) b3.add(w + nr * lay.vec_off[r.node], r.m, 1, {{r.Wt, r.s, xs + nr * goff[a], nullptr, r.s, false, T(-1)}});
+      b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+    }
+    b1.emit(P, s);
+    b2.emit(P, s);
+    if (!gidx.empty()) {
+      const size_t oi = P.b.push(gidx);
+      const int ng = (int)gidx.size(), r = nr;
+      const T* src = v;
+      P.acct.push_back({P_VECCOPY, 0.0, 2.0 * sizeof(T) * ng * r + 4.0 * ng});
+      P.ops.push_back([=](const char* d, cudaStream_t st) {
+        launch_vgather<T>(src, (const int*)(d + oi), xs, ng, r, st);
+      });
+    }
+    b3.emit(P, s);
+    b4.emit(P, s);
   }
 
   // y = A_l x: the factors applied in the opposite order (G^T, B^T up, top

@@ -52,12 +52,15 @@ struct Batch {
   size_t push(const std::vector<X>& v) {
     const size_t off = (host.size() + 63) & ~size_t(63);
     const size_t bytes = v.size() * sizeof(X);
-    if (host.capacity() < off + bytes) host.reserve(std::max(2 * host.capacity(), off + bytes));
+    if (host.capacity() < off + bytes) grow(std::max(2 * host.capacity(), off + bytes));
     host.insert(host.end(), off - host.size(), char(0));   // alignment padding only
     const char* p = reinterpret_cast<const char*>(v.data());
     host.insert(host.end(), p, p + bytes);
     return off;
   }
+  // move the staged bytes into a buffer of at least `want` bytes of capacity
+  // (a pooled one when one fits: its pages are already resident)
+  void grow(size_t want);
   // upload and run everything recorded so far, then reset
   void run(cudaStream_t s);
   // keep the uploaded copy (for programs replayed many times)

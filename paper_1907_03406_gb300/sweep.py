@@ -24,7 +24,7 @@ def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000):
 
     import sgf_inputs as si
 
-    from . import Factor, Plan
+    from . import Factor, Plan, release_cached_memory
 
     dev = torch.device("cuda", torch.cuda.current_device())
     rows = []
@@ -34,6 +34,7 @@ def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000):
         coeffs = torch.tensor(np.ascontiguousarray(cfg["coeffs"]).ravel(), dtype=torch.float64, device=dev)
         b = torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
+        release_cached_memory()   # the previous size's blocks, cached by the pool
         free0 = torch.cuda.mem_get_info()[0]
         t0 = time.perf_counter()
         F = Factor(plan, coeffs)
