@@ -194,9 +194,12 @@ def kernel_bound(name: str, precision: str, peaks: dict):
     return "alu", "TFLOP/s", 1.25, "nominal GB300 FP64 rate"
 
 
-def traffic_from_profiles(kernel: str):
-    """dram bytes per launch recorded from an ncu capture of this kernel, if any."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.txt")
+def traffic_from_profiles(kernel: str, precision: str = "mixed"):
+    """dram bytes per launch recorded from an ncu capture of this kernel on
+    this precision's path, if any (the summaries without a suffix are of the
+    mixed-precision path)."""
+    suffix = "" if precision == "mixed" else f"_{precision}"
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}{suffix}.txt")
     try:
         with open(path) as f:
             for line in f:
@@ -219,7 +222,7 @@ def roofline(prof: dict, precision: str, peaks: dict):
     else:
         achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 2),
-            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic_from_profiles(name),
+            "unit": unit, "frac": round(achieved / peak, 4), "traffic": traffic_from_profiles(name, precision),
             "launches": rec["launches"], "avg_launch_ms": round(per_launch_ms, 5),
             "share_of_step": None, "peak_note": note}
 

@@ -1758,23 +1758,24 @@ int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double 
   const int k = nrhs;
   if (k < 1 || k > 8) throw SgfError(SGF_ERR_INVALID_ARG, "block PCG takes 1..8 right-hand sides");
   const size_t kn = (size_t)k * n;
-  double* buf = (double*)dev_malloc_async(sizeof(double) * (5 * kn + 8 * kDotBlocks + 32), s);
+  double* buf = (double*)dev_malloc_async(sizeof(double) * (5 * kn + 8 * kDotBlocks + 64), s);
   double *r = buf, *z = r + kn, *p = z + kn, *q = p + kn, *ro = q + kn;
   double* part = ro + kn;
+  // device scalars, 8 per slot: 0 r.r | 1 r.z | 2 z.ro | 3 p.q | 4-5 alpha,
+  // -alpha | 6 non-finite alpha flags
   double* sc = part + 8 * kDotBlocks;
-  double h[32];
-  // one batch of nd dot products (each over k RHS), read back with one sync
-  auto dots = [&](std::initializer_list<std::pair<const double*, const double*>> ab) {
-    int j = 0;
-    for (const auto& pr : ab) launch_dot_n(pr.first, pr.second, n, k, part, sc + 8 * j++, s);
-    dev_d2h(h, sc, sizeof(double) * 8 * j, s);
-  };
+  double* coef = sc + 32;
+  double* flag = sc + 48;
+  double h[56];
+  auto dot = [&](const double* a, const double* bb, int slot) { launch_dot_n(a, bb, n, k, part, sc + 8 * slot, s); };
+  auto read = [&](int nslots) { dev_d2h(h, sc, sizeof(double) * 8 * nslots, s); };   // synchronizes
   const bool flex = F.mixed();
   std::vector<double> bnorm(k), rz(k);
   std::vector<char> active(k);
   dev_memset(x, 0, kn * sizeof(double), s);
   dev_d2d(r, b, kn * sizeof(double), s);
-  dots({{b, b}});
+  dot(b, b, 0);
+  read(1);
   for (int j = 0; j < k; ++j) {
     bnorm[j] = std::sqrt(h[j]);
     active[j] = bnorm[j] > 0.0;
@@ -1783,37 +1784,43 @@ int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double 
   int rc = SGF_OK;
   F.apply_n(r, z, k, s);
   dev_d2d(p, z, kn * sizeof(double), s);
-  dots({{r, z}});
-  for (int j = 0; j < k; ++j) rz[j] = h[j];
+  dot(r, z, 1);
+  read(2);
+  for (int j = 0; j < k; ++j) rz[j] = h[8 + j];
   int it = 0;
   auto any = [&] {
     for (int j = 0; j < k; ++j)
       if (active[j]) return true;
     return false;
   };
+  // one host synchronisation per iteration: the step length is formed on the
+  // device from the r.z and p.q in device memory; the host reads the
+  // residual norms, the new r.z and the flags once the preconditioner ran
   while (any()) {
     if (it >= maxit) { rc = SGF_ERR_NO_CONVERGENCE; break; }
     for (int j = 0; j < k; ++j) F.spmv(p + (size_t)j * n, q + (size_t)j * n, s);
-    dots({{p, q}});
-    Coef8 al{}, nal{};
-    for (int j = 0; j < k; ++j) {
-      const double a = active[j] ? rz[j] / h[j] : 0.0;
-      if (active[j] && !std::isfinite(a)) { rc = SGF_ERR_NONFINITE; active[j] = 0; continue; }
-      al.v[j] = active[j] ? a : 0.0;
-      nal.v[j] = -al.v[j];
-    }
-    launch_axpy_n(al, p, x, n, k, 0, s);
-    if (flex) dev_d2d(ro, r, kn * sizeof(double), s);
-    launch_axpy_n(nal, q, r, n, k, 0, s);
+    dot(p, q, 3);
+    Coef8 act{};
+    for (int j = 0; j < k; ++j) act.v[j] = active[j] ? 1.0 : 0.0;
+    launch_pcg_alpha(sc + 24, sc + 8, act, k, coef, flag, s);
+    launch_pcg_xr(coef, p, q, x, r, flex ? ro : nullptr, n, k, s);
     ++it;
     for (int j = 0; j < k; ++j)
       if (active[j]) iters[j] = it;
     F.apply_n(r, z, k, s);
-    if (flex) dots({{r, r}, {r, z}, {z, ro}});
-    else dots({{r, r}, {r, z}});
+    dot(r, r, 0);
+    dot(r, z, 1);
+    if (flex) dot(z, ro, 2);
+    read(7);
     Coef8 be{};
     for (int j = 0; j < k; ++j) {
       if (!active[j]) continue;
+      if (h[48 + j] != 0.0) {   // this iteration's step length was not finite: x_j, r_j unchanged
+        rc = SGF_ERR_NONFINITE;
+        active[j] = 0;
+        iters[j] = it - 1;
+        continue;
+      }
       if (std::sqrt(h[j]) <= rtol * bnorm[j]) { active[j] = 0; continue; }
       const double rzn = h[8 + j];
       be.v[j] = flex ? (rzn - h[16 + j]) / rz[j] : rzn / rz[j];
@@ -1827,7 +1834,8 @@ int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double 
   Coef8 m1{};
   for (int j = 0; j < k; ++j) m1.v[j] = -1.0;
   launch_axpy_n(m1, q, r, n, k, 0, s);
-  dots({{r, r}});
+  dot(r, r, 0);
+  read(1);
   for (int j = 0; j < k; ++j) relres[j] = bnorm[j] > 0 ? std::sqrt(h[j]) / bnorm[j] : 0.0;
   dev_free_async(buf, s);
   return rc;

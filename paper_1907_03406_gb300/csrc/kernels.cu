@@ -1489,6 +1489,31 @@ __global__ void k_axpy_n(Coef8 a, const double* __restrict__ x, double* __restri
   }
 }
 
+__global__ void k_pcg_alpha(const double* __restrict__ pq, const double* __restrict__ rz, Coef8 act, int nrhs,
+                            double* __restrict__ coef, double* __restrict__ flag) {
+  const int q = threadIdx.x;
+  if (q >= nrhs) return;
+  const double a = act.v[q] != 0.0 ? rz[q] / pq[q] : 0.0;
+  const bool bad = !isfinite(a);
+  coef[q] = bad ? 0.0 : a;
+  coef[8 + q] = bad ? 0.0 : -a;
+  flag[q] = bad ? 1.0 : 0.0;
+}
+
+__global__ void k_pcg_xr(const double* __restrict__ coef, const double* __restrict__ p,
+                         const double* __restrict__ qv, double* __restrict__ x, double* __restrict__ r,
+                         double* __restrict__ ro, int64_t n, int nrhs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < nrhs; ++q) {
+    const int64_t k = (int64_t)q * n + i;
+    const double rk = r[k];
+    x[k] = fma(coef[q], p[k], x[k]);
+    if (ro) ro[k] = rk;
+    r[k] = fma(coef[8 + q], qv[k], rk);
+  }
+}
+
 template <typename T>
 __global__ void k_gather(const double* __restrict__ src, const int64_t* __restrict__ perm,
                          T* __restrict__ dst, int64_t n, int nrhs, int nr) {
@@ -1887,6 +1912,21 @@ void launch_axpy_n(const Coef8& a, const double* x, double* y, int64_t n, int nr
   prof_work(2.0 * n * nrhs, 24.0 * n * nrhs);
   ProfScope ps(P_VEC, s);
   k_axpy_n<<<blocks_for(n), kThreads, 0, s>>>(a, x, y, n, nrhs, mode);
+}
+
+void launch_pcg_alpha(const double* pq, const double* rz, const Coef8& act, int nrhs, double* coef, double* flag,
+                      cudaStream_t s) {
+  if (dry_run() || nrhs <= 0) return;
+  ProfScope ps(P_VEC, s);
+  k_pcg_alpha<<<1, 32, 0, s>>>(pq, rz, act, nrhs, coef, flag);
+}
+
+void launch_pcg_xr(const double* coef, const double* p, const double* q, double* x, double* r, double* ro,
+                   int64_t n, int nrhs, cudaStream_t s) {
+  if (dry_run() || n <= 0 || nrhs <= 0) return;
+  prof_work(4.0 * n * nrhs, (ro ? 56.0 : 48.0) * n * nrhs);
+  ProfScope ps(P_VEC, s);
+  k_pcg_xr<<<blocks_for(n), kThreads, 0, s>>>(coef, p, q, x, r, ro, n, nrhs);
 }
 
 void launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s) {

@@ -115,6 +115,16 @@ void launch_dot_n(const double* a, const double* b, int64_t n, int nrhs, double*
 void launch_axpy_n(const Coef8& a, const double* x, double* y, int64_t n, int nrhs, int mode,
                    cudaStream_t s);
 
+// PCG step length on the device (Sec. 7): alpha_q = rz_q / pq_q where
+// act.v[q] != 0, else 0, written to coef[q] and -alpha_q to coef[8 + q];
+// flag[q] = 1 (else 0) where alpha_q is not finite, its coefficients then 0
+void launch_pcg_alpha(const double* pq, const double* rz, const Coef8& act, int nrhs, double* coef,
+                      double* flag, cudaStream_t s);
+// x_q += alpha_q p_q; ro_q = r_q (when ro is given); r_q -= alpha_q q_q, with
+// alpha_q = coef[q] and -alpha_q = coef[8 + q] read on the device
+void launch_pcg_xr(const double* coef, const double* p, const double* q, double* x, double* r, double* ro,
+                   int64_t n, int nrhs, cudaStream_t s);
+
 // y = a*x + y (FP64)
 void launch_axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s);
 // p = z + b*p (FP64)
