@@ -1449,9 +1449,8 @@ class FactorImpl final : public FactorBase {
   static constexpr int kMaxNr = 8;
   // level-vector buffers [v | w | kept] of non-top level t
   void ensure_vb(int t, int64_t vec_size, cudaStream_t s) {
-    if ((int)vb_.size() > t) return;
-    vb_.resize(t + 1, nullptr);
-    vb_[t] = dalloc<T>(keep_, 3 * (size_t)kMaxNr * std::max<int64_t>(vec_size, 1), s);
+    if ((int)vb_.size() <= t) vb_.resize(t + 1, nullptr);
+    if (!vb_[t]) vb_[t] = dalloc<T>(keep_, 3 * (size_t)kMaxNr * std::max<int64_t>(vec_size, 1), s);
   }
   // While the GPU factors level t + 1 (vec_size: its vector length), the host
   // records the single-RHS inverse program's parts for the finished level t.
@@ -1463,7 +1462,7 @@ class FactorImpl final : public FactorBase {
   }
   void build_programs(cudaStream_t s) {
     const int nl = (int)lev_.size();
-    for (int t = (int)vb_.size(); t < nl; ++t) ensure_vb(t, lev_[t].lay.vec_size, s);
+    for (int t = 0; t < nl; ++t) ensure_vb(t, lev_[t].lay.vec_size, s);
     vtop_ = dalloc<T>(keep_, 2 * (size_t)kMaxNr * std::max(mtop_, 1), s);
     program(true, 1, s);   // the forward (multiply) programs are built on first use
   }
