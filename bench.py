@@ -244,9 +244,10 @@ def run_ours(args):
     coeffs = torch.tensor(coeffs_h, dtype=torch.float64, device=dev)
     b = torch.tensor(b_h, dtype=torch.float64, device=dev)
     plans = {p: sgf.Plan.from_config(cfg, precision=p) for p in ("mixed", "fp64")}
-    # launch shapes from the autotuner (untimed setup: one factor + 10 applies
-    # per candidate), reported in config.tuning
-    tuned = {p: plans[p].autotune(coeffs, napply=10)[0] for p in plans}
+    # launch shapes from the autotuner (untimed setup: factor shapes timed on
+    # factorizations, GEMV budgets on 20 applies each), reported in
+    # config.tuning
+    tuned = {p: plans[p].autotune(coeffs, napply=20)[0] for p in plans}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream()
 

@@ -153,14 +153,18 @@ int sgf_plan_get_tuning(const sgf_plan* plan, sgf_tuning* out);
 /* Replace the tuning of a plan; INVALID_ARG (plan unchanged) when a field is
  * outside the ranges above.  Factors made before keep their launch shapes.  */
 int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t);
-/* Autotuner: for each candidate of a small grid of tunings (GEMV budgets x,
- * in single precision, front_small x tensor_cores; the defaults included),
- * times with CUDA events on `stream` one sgf_factor of coeffs_dev plus
- * napply applications of A_l^{-1} (napply >= 0) to a fixed vector, after one
- * untimed warm-up factorization, and keeps the fastest in the plan.  Writes
- * it to *best and its time (ms) to *best_ms when not NULL.  Allocates and
- * frees device memory; synchronizes the stream.  Errors: those of
- * sgf_factor; on error the plan keeps its previous tuning.                  */
+/* Autotuner: searches the launch shapes with CUDA events on `stream`, after
+ * one untimed warm-up factorization of coeffs_dev.  First, in single
+ * precision, front_small x tensor_cores (512/256 x 1/0), each timed as the
+ * faster of two sgf_factor calls; then, with the fastest of those, five GEMV
+ * budgets (4K-32K, 8K-64K, 16K-128K, 32K-128K, 32K-256K elements per task),
+ * each timed on napply applications of A_l^{-1} to a fixed vector (skipped
+ * when napply = 0: the budgets stay as they were).  The two groups are
+ * independent (the first changes only the factorization, the second only
+ * the apply).  Keeps the result in the plan, writes it to *best and the sum
+ * of the two best times (ms) to *best_ms when not NULL.  Allocates and frees
+ * device memory; synchronizes the stream.  Errors: those of sgf_factor; on
+ * error the plan keeps its previous tuning.                                 */
 int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int napply, sgf_tuning* best,
                  double* best_ms);
 

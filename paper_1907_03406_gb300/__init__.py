@@ -132,9 +132,9 @@ class Plan:
         _check(self._lib.sgf_plan_set_tuning(self.handle, C.byref(t)), "sgf_plan_set_tuning")
 
     def autotune(self, coeffs, napply: int = 10, stream=None):
-        """Grid search of the launch shapes on one factorization + napply
-        applies (sgf_autotune); keeps the fastest in the plan and returns
-        (tuning dict, ms)."""
+        """Search of the launch shapes (sgf_autotune): factor shapes timed on
+        factorizations, GEMV budgets on napply applies; keeps the fastest in
+        the plan and returns (tuning dict, factor + apply ms)."""
         t, ms = L.sgf_tuning(), C.c_double()
         _check(self._lib.sgf_autotune(self.handle, _dev_ptr(coeffs), _stream_ptr(stream), int(napply),
                                       C.byref(t), C.byref(ms)), "sgf_autotune")

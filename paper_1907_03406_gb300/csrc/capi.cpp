@@ -129,8 +129,12 @@ int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t) {
   return SGF_OK;
 }
 
-// Grid search over launch shapes: each candidate is timed on one factorization
-// plus napply applications of A_l^{-1}, the fastest is kept.
+// Grid search over launch shapes.  The factor shapes (front_small x
+// tensor_cores, single precision only) change only the factorization and the
+// GEMV budgets only the apply programs, so they are searched one after the
+// other: each factor shape by the faster of two timed factorizations, then,
+// with the best one, each GEMV budget by napply timed applications of
+// A_l^{-1} (its factorization untimed).
 int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int napply, sgf_tuning* best,
                  double* best_ms) {
   if (!plan || !coeffs_dev || napply < 0) return SGF_ERR_INVALID_ARG;
@@ -139,16 +143,6 @@ int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int nap
   const int rc = guarded([&] {
     cudaStream_t s = (cudaStream_t)stream;
     const bool mixed = plan->p.opts.precision == SGF_PREC_MIXED;
-    std::vector<sgf_tuning> cand;
-    const int budgets[3][2] = {{4096, 32768}, {8192, 65536}, {16384, 131072}};
-    for (const auto& bgt : budgets) {
-      if (mixed) {
-        for (int tc : {1, 0})
-          for (int fs : {512, 256}) cand.push_back({bgt[0], bgt[1], fs, tc});
-      } else {
-        cand.push_back({bgt[0], bgt[1], saved.front_small, saved.tensor_cores});
-      }
-    }
     const int64_t n = plan->p.n;
     double* x = (double*)sgf::dev_malloc(sizeof(double) * n);
     double* y = (double*)sgf::dev_malloc(sizeof(double) * n);
@@ -166,33 +160,72 @@ int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int nap
       }
     } cleanup{x, y, e0, e1};
     sgf::dev_memset(x, 0, sizeof(double) * n, s);   // any fixed vector times the same
+    auto elapsed = [&] {
+      SGF_CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      SGF_CK(cudaEventElapsedTime(&ms, e0, e1));
+      return (double)ms;
+    };
     {
-      plan->p.tune = cand[0];   // warm-up: caches, pools, module loading
-      auto f = sgf::make_factor(plan->p, coeffs_dev, s);
+      auto f = sgf::make_factor(plan->p, coeffs_dev, s);   // warm-up: caches, pools, module loading
       if (napply > 0) f->apply(x, y, s);
       sgf::dev_sync(s);
     }
-    double best_t = 1e300;
-    sgf_tuning best_c = saved;
-    for (const sgf_tuning& c : cand) {
-      plan->p.tune = c;
-      SGF_CK(cudaEventRecord(e0, s));
-      {
+    sgf_tuning cur = saved;
+    double t_factor = 0;
+    {
+      std::vector<std::pair<int, int>> shapes;   // (front_small, tensor_cores)
+      if (mixed) {
+        for (int tc : {1, 0})
+          for (int fs : {512, 256}) shapes.push_back({fs, tc});
+      } else {
+        shapes.push_back({saved.front_small, saved.tensor_cores});
+      }
+      double bt = 1e300;
+      for (const auto& sh : shapes) {
+        plan->p.tune = saved;
+        plan->p.tune.front_small = sh.first;
+        plan->p.tune.tensor_cores = sh.second;
+        double t = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+          SGF_CK(cudaEventRecord(e0, s));
+          auto f = sgf::make_factor(plan->p, coeffs_dev, s);
+          SGF_CK(cudaEventRecord(e1, s));
+          t = std::min(t, elapsed());
+        }
+        if (t < bt) {
+          bt = t;
+          cur = plan->p.tune;
+        }
+      }
+      t_factor = bt;
+    }
+    double t_apply = 0;
+    if (napply > 0) {
+      const int budgets[5][2] = {{4096, 32768}, {8192, 65536}, {16384, 131072}, {32768, 131072}, {32768, 262144}};
+      double bt = 1e300;
+      sgf_tuning bc = cur;
+      for (const auto& bgt : budgets) {
+        plan->p.tune = cur;
+        plan->p.tune.gemv_min_elems = bgt[0];
+        plan->p.tune.gemv_max_elems = bgt[1];
         auto f = sgf::make_factor(plan->p, coeffs_dev, s);
+        f->apply(x, y, s);   // first use: the program's graph is captured
+        SGF_CK(cudaEventRecord(e0, s));
         for (int k = 0; k < napply; ++k) f->apply(x, y, s);
         SGF_CK(cudaEventRecord(e1, s));
-        SGF_CK(cudaEventSynchronize(e1));
+        const double t = elapsed();
+        if (t < bt) {
+          bt = t;
+          bc = plan->p.tune;
+        }
       }
-      float ms = 0;
-      SGF_CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_t) {
-        best_t = ms;
-        best_c = c;
-      }
+      cur = bc;
+      t_apply = bt;
     }
-    plan->p.tune = best_c;
-    if (best) *best = best_c;
-    if (best_ms) *best_ms = best_t;
+    plan->p.tune = cur;
+    if (best) *best = cur;
+    if (best_ms) *best_ms = t_factor + t_apply;
     return (int)SGF_OK;
   });
   if (rc != SGF_OK) plan->p.tune = saved;
