@@ -1489,6 +1489,8 @@ __global__ void k_axpy_n(Coef8 a, const double* __restrict__ x, double* __restri
   }
 }
 
+// PCG step length per right-hand side q (one thread each): rz_q / pq_q where
+// active, 0 where not or where the quotient is not finite (flagged)
 __global__ void k_pcg_alpha(const double* __restrict__ pq, const double* __restrict__ rz, Coef8 act, int nrhs,
                             double* __restrict__ coef, double* __restrict__ flag) {
   const int q = threadIdx.x;
@@ -1500,6 +1502,8 @@ __global__ void k_pcg_alpha(const double* __restrict__ pq, const double* __restr
   flag[q] = bad ? 1.0 : 0.0;
 }
 
+// x_q += alpha_q p_q, ro_q = r_q (optional), r_q -= alpha_q q_q in one pass,
+// alpha_q and -alpha_q read from device memory
 __global__ void k_pcg_xr(const double* __restrict__ coef, const double* __restrict__ p,
                          const double* __restrict__ qv, double* __restrict__ x, double* __restrict__ r,
                          double* __restrict__ ro, int64_t n, int nrhs) {
