@@ -140,12 +140,15 @@ int sgf_plan_footprint(const sgf_plan* plan, size_t* bytes_fp64, size_t* bytes_m
  *     a batch of at least one front per SM (single precision); 64..512.
  *   tensor_cores: 1 = single-precision factor GEMMs on the tensor cores as
  *     3xTF32 split products, 0 = FP32 CUDA cores.
- * Defaults: 4096, 32768, 512, 1.                                             */
+ *   gemv_cols: outputs per apply GEMV task of the transposed (column dot
+ *     product) form, 32 or 64 (single precision; double precision uses 32).
+ * Defaults: 4096, 32768, 512, 1, 32.                                         */
 typedef struct {
   int gemv_min_elems;
   int gemv_max_elems;
   int front_small;
   int tensor_cores;
+  int gemv_cols;
 } sgf_tuning;
 
 /* Current tuning of a plan (INVALID_ARG on NULL). */
@@ -158,7 +161,8 @@ int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t);
  * precision, front_small x tensor_cores (512/256 x 1/0), each timed as the
  * faster of two sgf_factor calls; then, with the fastest of those, five GEMV
  * budgets (4K-32K, 8K-64K, 16K-128K, 32K-128K, 32K-256K elements per task),
- * each timed on napply applications of A_l^{-1} to a fixed vector (skipped
+ * in single precision each with gemv_cols 32 and 64, each timed on napply
+ * applications of A_l^{-1} to a fixed vector (skipped
  * when napply = 0: the budgets stay as they were).  The two groups are
  * independent (the first changes only the factorization, the second only
  * the apply).  Keeps the result in the plan, writes it to *best and the sum

@@ -18,7 +18,7 @@ class sgf_grid(C.Structure):
 
 class sgf_tuning(C.Structure):
     _fields_ = [("gemv_min_elems", C.c_int), ("gemv_max_elems", C.c_int), ("front_small", C.c_int),
-                ("tensor_cores", C.c_int)]
+                ("tensor_cores", C.c_int), ("gemv_cols", C.c_int)]
 
 
 class sgf_opts(C.Structure):

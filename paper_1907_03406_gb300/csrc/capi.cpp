@@ -133,8 +133,9 @@ int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t) {
 // tensor_cores, single precision only) change only the factorization and the
 // GEMV budgets only the apply programs, so they are searched one after the
 // other: each factor shape by the faster of two timed factorizations, then,
-// with the best one, each GEMV budget by napply timed applications of
-// A_l^{-1} (its factorization untimed).
+// with the best one, each GEMV budget (x op T chunk width in single
+// precision) by napply timed applications of A_l^{-1} (its factorization
+// untimed).
 int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int napply, sgf_tuning* best,
                  double* best_ms) {
   if (!plan || !coeffs_dev || napply < 0) return SGF_ERR_INVALID_ARG;
@@ -203,12 +204,19 @@ int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int nap
     double t_apply = 0;
     if (napply > 0) {
       const int budgets[5][2] = {{4096, 32768}, {8192, 65536}, {16384, 131072}, {32768, 131072}, {32768, 262144}};
+      std::vector<sgf_tuning> cand;
+      for (int cols : mixed ? std::vector<int>{32, 64} : std::vector<int>{saved.gemv_cols})
+        for (const auto& bgt : budgets) {
+          sgf_tuning c = cur;
+          c.gemv_min_elems = bgt[0];
+          c.gemv_max_elems = bgt[1];
+          c.gemv_cols = cols;
+          cand.push_back(c);
+        }
       double bt = 1e300;
       sgf_tuning bc = cur;
-      for (const auto& bgt : budgets) {
-        plan->p.tune = cur;
-        plan->p.tune.gemv_min_elems = bgt[0];
-        plan->p.tune.gemv_max_elems = bgt[1];
+      for (const sgf_tuning& c : cand) {
+        plan->p.tune = c;
         auto f = sgf::make_factor(plan->p, coeffs_dev, s);
         f->apply(x, y, s);   // first use: the program's graph is captured
         SGF_CK(cudaEventRecord(e0, s));

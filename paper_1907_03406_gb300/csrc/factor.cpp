@@ -190,7 +190,7 @@ struct TuneScope {
   ~TuneScope() { t_tune = prev; }
 };
 inline const sgf_tuning& active_tuning() {
-  static const sgf_tuning def{4096, 32768, 512, 1};
+  static const sgf_tuning def{4096, 32768, 512, 1, 32};
   return t_tune ? *t_tune : def;
 }
 
@@ -539,6 +539,8 @@ struct GemvList {
   std::vector<GemvContrib<T>> c;
   bool trans = false;
   int nr = 1;  // interleaved right-hand sides
+  // op T chunk width: the tuning's in single precision, kGemvCols in double
+  const int cols = std::is_same<T, float>::value ? active_tuning().gemv_cols : kGemvCols;
   explicit GemvList(int nr_ = 1) : nr(nr_) {}
   struct In {
     const T* A;
@@ -551,10 +553,10 @@ struct GemvList {
     bool upper = false;   // tri: the upper triangle (op T: rows <= column)
   };
   // y[M] = beta y + sum alpha op(A)(x - x2); op N chunks of kGemvBand rows,
-  // op T chunks of kGemvCols columns (one unsplit task each until emit)
+  // op T chunks of `cols` columns (one unsplit task each until emit)
   void add(T* y, int M, int beta, const std::vector<In>& ins) {
     if (M <= 0) return;
-    const int chunk = trans ? kGemvCols : kGemvBand;
+    const int chunk = trans ? cols : kGemvBand;
     for (int i0 = 0; i0 < M; i0 += chunk) {
       GemvTask<T> g{};
       g.y = y + (size_t)i0 * nr;
@@ -701,13 +703,13 @@ struct GemvList {
     const size_t ot = P.b.push(tasks), oc = P.b.push(c);
     const int n = (int)tasks.size();
     const bool tr = trans;
-    const int r = nr;
+    const int r = nr, cw = cols;
     int max_m = 1;
     for (const auto& h : tasks) max_m = std::max(max_m, h.M);
     P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl * r, by});
     P.ops.push_back([=](const char* d, cudaStream_t st) {
       prof_work(fl * r, by);
-      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, st);
+      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, cw, st);
       else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, max_m, st);
     });
     t.clear();

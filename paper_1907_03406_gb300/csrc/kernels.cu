@@ -1180,16 +1180,15 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restri
   gemv_finish(tk, tk.M * NR);
 }
 
-// op(A) = A^T: <= kGemvCols outputs, column o of A handled by warp o % 8
-// (four columns per warp, their loads interleaved).  The task's column
+// op(A) = A^T: <= 8 CW outputs, column o of A handled by warp o % 8 (CW
+// columns per warp, their loads interleaved).  The task's column
 // segments are prefetched into L2 first; lanes then stride over the flat rows
 // of each contribution, and the lane sums are combined by a butterfly.
-template <typename T, int NR>
+template <typename T, int NR, int CW>
 __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
     k_gemv_t(const GemvTask<T>* __restrict__ tasks,
                                                      const GemvContrib<T>* __restrict__ cons) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int CW = kGemvCols / kWarps;
   pdl_trigger();
   const GemvTask<T> tk = tasks[blockIdx.x];
   __shared__ GemvStage<T> S;
@@ -1222,7 +1221,7 @@ __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
       const T* a = cb.A + (size_t)w * cb.lda;
       const size_t cstep = (size_t)kWarps * cb.lda;
       const int cmin = cb.tri ? cb.tri - 1 + w : 0;   // absolute column of u = 0
-      constexpr int kUnroll = (sizeof(T) == 4 && NR <= 2) ? 4 : 2;   // row steps in flight
+      constexpr int kUnroll = (sizeof(T) == 4 && NR <= 2 && CW <= 4) ? 4 : 2;   // row steps in flight
 #pragma unroll kUnroll
       for (int i = i0 + lane; i < i1; i += 32) {
         T xv[NR];
@@ -1698,7 +1697,7 @@ static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int
                        int max_m) {
   for (int i = 0; i < n; ++i) {
     const GemvTask<T>& t = tasks[i];
-    if (t.M > (trans ? kGemvCols : kGemvBand) || t.M < 1 || t.M > max_m) check_range(nullptr, 1, "gemv chunk shape");
+    if (t.M > (trans ? kGemvColsMax : kGemvBand) || t.M < 1 || t.M > max_m) check_range(nullptr, 1, "gemv chunk shape");
     if (t.c_count < 0 || t.c_count > kGemvMaxC) check_range(nullptr, 1, "gemv contribution count");
     check_range(t.y, sizeof(T) * t.M * nr, "gemv y");
     int total = 0;
@@ -1781,16 +1780,29 @@ void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, 
   }
 }
 
+// the 64-wide chunks exist in single precision only (double-precision
+// accumulators of 8 columns x 8 right-hand sides would not fit the registers)
+template <typename T, int NR>
+static void gemv_t_cw(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int cols, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (cols > kGemvCols) {
+      launch_apply_kernel(k_gemv_t<T, NR, kGemvColsMax / (kThreads / 32)>, n, s, tasks, cons);
+      return;
+    }
+  }
+  launch_apply_kernel(k_gemv_t<T, NR, kGemvCols / (kThreads / 32)>, n, s, tasks, cons);
+}
+
 template <typename T>
-void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, true, nr, kGemvCols);
+void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, int cols, cudaStream_t s) {
+  if (dry_run()) return check_gemv(tasks, cons, n, true, nr, cols);
   if (n <= 0) return;
   ProfScope ps(P_GEMV_T, s);
   switch (nr) {
-    case 1: launch_apply_kernel(k_gemv_t<T, 1>, n, s, tasks, cons); break;
-    case 2: launch_apply_kernel(k_gemv_t<T, 2>, n, s, tasks, cons); break;
-    case 4: launch_apply_kernel(k_gemv_t<T, 4>, n, s, tasks, cons); break;
-    default: launch_apply_kernel(k_gemv_t<T, 8>, n, s, tasks, cons); break;
+    case 1: gemv_t_cw<T, 1>(tasks, cons, n, cols, s); break;
+    case 2: gemv_t_cw<T, 2>(tasks, cons, n, cols, s); break;
+    case 4: gemv_t_cw<T, 4>(tasks, cons, n, cols, s); break;
+    default: gemv_t_cw<T, 8>(tasks, cons, n, cols, s); break;
   }
 }
 
@@ -1957,7 +1969,7 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
                                cudaStream_t);                                                    \
   template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int, int,      \
                                  cudaStream_t);                                                  \
-  template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int,           \
+  template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int, int,      \
                                  cudaStream_t);                                                  \
   template void launch_veccopy<T>(const VecCopyTask*, int, const T*, T*, cudaStream_t);         \
   template void launch_vgather<T>(const T*, const int*, T*, int, int, cudaStream_t);           \

@@ -63,8 +63,10 @@ size_t qr_smem_bytes(int m, int c, size_t elem_size, long long cap_elems);
 template <typename T>
 void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr, int max_m,
                    cudaStream_t s);
+// cols: the chunk width the tasks were built with (kGemvCols, or
+// kGemvColsMax in single precision)
 template <typename T>
-void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr,
+void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr, int cols,
                    cudaStream_t s);
 // dst[p * nr + q] = src[idx[p] * nr + q], p < n
 template <typename T>

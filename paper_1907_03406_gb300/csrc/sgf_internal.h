@@ -74,7 +74,7 @@ struct Plan {
   std::vector<int64_t> asm_map, perm1;
   std::vector<int> asm_ld;         // Q1: level-1 node size of every point
   // launch shapes (sgf_tuning; see sgf_plan_set_tuning)
-  sgf_tuning tune{4096, 32768, 512, 1};
+  sgf_tuning tune{4096, 32768, 512, 1, 32};
 
   // device copies of the plan's constant data, built on first use
   struct DevCache {
@@ -175,7 +175,8 @@ struct QrTask {          // column-pivoted Householder QR of A (m x c, ld = m)
 
 // Batched GEMV.  A chunk is y[M] = beta*y + sum_c alpha_c op(A_c) (x_c - x2_c)
 // over its contributions c; op N chunks are bands of <= kGemvBand rows, op T
-// chunks hold <= kGemvCols columns of A; one CTA works on one task.  The
+// chunks hold 32 or 64 (kGemvColsMax, a tuning choice in single precision)
+// columns of A; one CTA works on one task.  The
 // contributions' useful indices (columns for op N, rows for op T; see
 // gemv_useful) are concatenated into one flat range, and a chunk may be split
 // into nsplit pieces of that range, each a task.  A split task writes its
@@ -183,7 +184,8 @@ struct QrTask {          // column-pivoted Householder QR of A (m x c, ld = m)
 // atomic counter) adds the partials in split order and writes y, so the
 // result does not depend on scheduling.
 constexpr int kGemvBand = 512;
-constexpr int kGemvCols = 32;
+constexpr int kGemvCols = 32;      // op T chunk width in double precision and by default
+constexpr int kGemvColsMax = 64;
 constexpr int kGemvMaxC = 32;   // contributions per task
 
 template <typename T>

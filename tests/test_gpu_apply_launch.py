@@ -84,3 +84,28 @@ def test_profile_counts_apply_replays_and_their_kernels():
     assert p["apply"]["bytes"] == pytest.approx(node_bytes, rel=1e-12)
     sgf.profile_reset(timing=False)
     F.close()
+
+
+def test_wide_gemv_chunks_match_the_default_and_stay_rhs_independent():
+    # gemv_cols = 64 only regroups the column dot products into wider tasks:
+    # every column's sum runs over the same rows in the same lane order, so
+    # the apply stays within rounding of the 32-wide one, and k right-hand
+    # sides still give exactly the single-RHS answers
+    cfg = si.config("grf3d_24")
+    dev = torch.device("cuda:0")
+    c = torch.tensor(cfg["coeffs"].ravel(), dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(11)
+    plan = sgf.Plan.from_config(cfg, precision="mixed")
+    X = rng.standard_normal((3, plan.n))
+    F32 = sgf.Factor(plan, c)
+    y32 = F32.apply(torch.tensor(X[0], device=dev)).cpu().numpy()
+    F32.close()
+    plan.tuning = {"gemv_cols": 64}
+    F = sgf.Factor(plan, c)
+    Y = F.apply(torch.tensor(X.ravel(), device=dev)).cpu().numpy().reshape(3, plan.n)
+    for j in range(3):
+        assert np.array_equal(Y[j], F.apply(torch.tensor(X[j], device=dev)).cpu().numpy())
+    assert np.linalg.norm(Y[0] - y32) <= 1e-5 * np.linalg.norm(y32)
+    x, info = F.pcg(torch.tensor(si.rhs(plan.n, 0), device=dev), rtol=1e-10, maxit=500)
+    assert info["rel_residual"] <= 1e-10
+    F.close()
