@@ -26,7 +26,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .basis import Basis
-from .sgf import Options, _eligible, dof_list, point_coords
+from .sgf import Options, _eligible, adjacent_low, dof_list, point_coords
 
 
 def _cell_dofs(H, box):
@@ -87,11 +87,14 @@ def dense_sgf(A, H, opts: Options = Options()):
             FT = F.T
             cols = [L.T @ (FT @ Pi_of(lev, B))[s]]
             o = 0
+            adj = []
             for X in others_nodes:
                 k = len(slots[X])
                 cols.append(Mh[:, o:o + k] @ (FT @ Pi_of(lev, X))[slots[X]])
+                if opts.scheme == "nest_2_2" and adjacent_low(lev, B, X, H.dim):
+                    adj.append(Mh[:, o:o + k])   # kept exactly: whole block in span(Q1)
                 o += k
-            Nmat = np.hstack(cols)
+            Nmat = np.hstack(cols + adj)
             Q, R, _ = sla.qr(Nmat, pivoting=True)
             d = np.abs(np.diag(R))
             r = int(np.sum(d > opts.tau * d[0]))

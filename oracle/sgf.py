@@ -31,6 +31,11 @@ Readings (the paper leaves these open):
 * tau = 1e-12 relative to |R_11| (the paper only says "e.g. pivoted QR");
 * 0-cells are never compressed (Sec. 5.1 notes it makes no difference);
 * Nest-2-All compresses only separators of codimension 1;
+* Nest-2-2 (Sec. 5.1) compresses the same nodes, with the scaled blocks
+  M^_BE = L^{-1} A_BE to every lower-dimensional separator E whose box
+  touches B's (at most one grid step apart on every axis) appended to N as
+  whole columns, so span(Q1) holds them and those interactions are kept
+  exactly; one pivoted QR with the usual rank rule gives Q1;
 * scheme "none" disables compression, which gives exact block Cholesky;
 * Gen-All-All (Sec. 5.2) runs on general partitions
   (build_hierarchy(general=True)): no interiors, every node is compressed.
@@ -48,7 +53,7 @@ from .partition import Hierarchy
 
 @dataclass
 class Options:
-    scheme: str = "nest_all_all"     # "nest_all_all" | "nest_2_all" | "gen_all_all" | "none"
+    scheme: str = "nest_all_all"     # "nest_all_all" | "nest_2_all" | "nest_2_2" | "gen_all_all" | "none"
     tau: float = 1e-12
     compress_from_level: int = 1
     basis: str = "poly"              # "poly" | "rbm"
@@ -66,11 +71,22 @@ def _eligible(lev, i, dim, opts: Options) -> bool:
     cd = int(lev.cell_dim[i])
     if opts.scheme == "nest_all_all":
         return cd >= 1
-    if opts.scheme == "nest_2_all":
+    if opts.scheme in ("nest_2_all", "nest_2_2"):
         return cd == dim - 1
     if opts.scheme == "gen_all_all":   # Sec. 5.2: every node of a general partition
         return True
     raise ValueError(opts.scheme)
+
+
+def adjacent_low(lev, B, X, dim) -> bool:
+    """Nest-2-2: X is a separator of lower dimension than the compressed
+    cells (cell_dim < dim - 1) whose box touches B's box."""
+    if lev.interior[X] or int(lev.cell_dim[X]) >= dim - 1:
+        return False
+    lo_b, hi_b = lev.box[B]
+    lo_x, hi_x = lev.box[X]
+    gap = np.maximum(0, np.maximum(lo_x - hi_b, lo_b - hi_x))
+    return bool(np.all(gap <= 1))
 
 
 def _get(blk, u, v):
@@ -182,13 +198,19 @@ class SGFFactor:
                 N_list = sorted(nbr[B])
                 L = self._chol(_get(src_blk, B, B))
                 Mh = [sla.solve_triangular(L, _get(src_blk, B, N), lower=True) for N in N_list]
-                Nmat = np.hstack([L.T @ src_phi[B]] + [Mh[k] @ src_phi[N] for k, N in enumerate(N_list)])
+                cols = [L.T @ src_phi[B]] + [Mh[k] @ src_phi[N] for k, N in enumerate(N_list)]
+                adj = [Mh[k] for k, N in enumerate(N_list)
+                       if opts.scheme == "nest_2_2" and adjacent_low(lev, B, N, H.dim)]
+                Nmat = np.hstack(cols + adj)
                 if opts.qr_noise > 0:
                     Nmat = Nmat * (1.0 + opts.qr_noise * noise_rng.standard_normal(Nmat.shape))
                 Q, R, _ = sla.qr(Nmat, pivoting=True)
                 d = np.abs(np.diag(R))
                 r = int(np.sum(d > opts.tau * d[0])) if d.size and d[0] > 0 else 0
+                A_adj = np.hstack(adj) if adj else np.zeros((m, 0))
                 info = dict(m=m, r=r, ncols=Nmat.shape[1], nnorm=float(np.linalg.norm(Nmat)),
+                            adj_cols=A_adj.shape[1], adj_norm=float(np.linalg.norm(A_adj)),
+                            adj_q2=float(np.linalg.norm(Q[:, r:].T @ A_adj)) if r < m else 0.0,
                             rdiag=d / d[0] if d.size and d[0] > 0 else d,
                             q2n=float(np.linalg.norm(Q[:, r:].T @ Nmat)) if r < m else 0.0,
                             compressed=r < m)

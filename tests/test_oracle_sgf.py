@@ -10,6 +10,10 @@ P5  explicit dense G_i, B_i restatement reproduces A_l (Sec. 2.1, Eq. (M')).
 P6  compressions inside a level commute (random order == canonical order).
 P7  trends: near-flat CG counts in n; higher degree => fewer iterations;
     E_n = ||(A - A_l) v_n|| / lambda_n stays O(1) (Table 5.1).
+Gen-All-All (Sec. 5.2): P1, P2/P4 and P5 on general partitions.
+Nest-2-2 (Sec. 5.1): blocks to touching lower-dimensional separators kept
+    exactly (Q2^T M^_BE = 0), P2/P4, level-1 ranks not below Nest-2-All's,
+    the paper's accuracy order of the nested schemes, and P5.
 """
 import numpy as np
 import pytest
@@ -268,6 +272,77 @@ def test_gen_P5_dense_brute_force_reproduces_block_oracle(n, seed, deg):
     Ad, _, ranks = dense_sgf(A, H, opts)
     assert ranks == F.ranks()
     assert any(v[2] for v in ranks.values())
+    Al = F.dense_operator()
+    assert np.abs(Al - Ad).max() <= 1e-12 * np.abs(Ad).max()
+    assert np.linalg.eigvalsh(0.5 * (Ad + Ad.T))[0] > 0
+
+
+# --------------------------------------------------------------------------
+# Nest-2-2 (Sec. 5.1): codimension-1 separators compressed with the span of
+# their blocks to the touching lower-dimensional separators added to Q1, so
+# only their interactions with non-adjacent cells are compressed; the paper
+# ranks it the most accurate nested scheme.
+# --------------------------------------------------------------------------
+def _grf24(scheme):
+    cfg = si.config("grf3d_24")
+    A = assemble(cfg)
+    H = build_hierarchy(cfg["n"], 3, 8, cfg["stencil"])
+    return A, H, factorize(A, H, Options(degree=2, scheme=scheme))
+
+
+def test_n22_adjacent_blocks_are_kept_exactly_and_polynomials_preserved():
+    A, H, F = _grf24("nest_2_2")
+    with_adj = [i for i in F.comp_info.values() if i["adj_cols"] > 0 and i["compressed"]]
+    assert with_adj, "some compressed node must touch a lower-dimensional separator"
+    for i in with_adj:   # Q2^T M^_BE = 0: the fine part does not see E
+        assert i["adj_q2"] <= 1e-12 * i["adj_norm"]
+    assert F.pivots_min > 0
+    Pi = _global_poly(H, 2)
+    AP = A @ Pi
+    err = np.linalg.norm(np.stack([F.multiply(Pi[:, k]) for k in range(Pi.shape[1])], 1) - AP)
+    assert err <= 1e-12 * np.linalg.norm(AP)
+
+
+def test_n22_level_one_ranks_contain_nest_2_all_ranks():
+    # at level 1 both schemes compress the same nodes of the same matrix and
+    # Nest-2-2's N holds Nest-2-All's columns plus more: its rank is not lower
+    _, H, F2 = _grf24("nest_2_all")
+    _, _, F22 = _grf24("nest_2_2")
+    r2, r22 = F2.ranks(), F22.ranks()
+    lvl1 = [k for k in r2 if k[0] == 1]
+    assert lvl1
+    assert all(r22[k][1] >= r2[k][1] for k in lvl1)
+    assert any(r22[k][1] > r2[k][1] for k in lvl1)
+
+
+def test_n22_most_accurate_of_the_nested_schemes():
+    # Sec. 5.1 orders the schemes Nest-All-All < Nest-2-All < Nest-2-2 in
+    # accuracy: fewer PCG iterations, and a smaller condition number of
+    # A_l^{-1} A on a grid small enough to form both densely
+    A, H, _ = _grf24("nest_2_2")
+    b = si.rhs(A.shape[0], 0)
+    its = {}
+    for sch in ("nest_all_all", "nest_2_all", "nest_2_2"):
+        F = factorize(A, H, Options(degree=2, scheme=sch))
+        _, its[sch], res = pcg(lambda v: A @ v, F.solve, b, rtol=1e-10)
+        assert res <= 1e-10
+    assert its["nest_2_2"] < its["nest_2_all"] <= its["nest_all_all"]
+    A, H = _grid_problem((13, 11, 9), 3, 4, "7pt_fv_3d", seed=1)
+    Ad = A.toarray()
+    cond = {}
+    for sch in ("nest_2_all", "nest_2_2"):
+        ev = sla.eigvalsh(Ad, factorize(A, H, Options(degree=1, scheme=sch)).dense_operator())
+        cond[sch] = ev.max() / ev.min()
+    assert cond["nest_2_2"] < cond["nest_2_all"]
+
+
+def test_n22_dense_brute_force_reproduces_block_oracle():
+    A, H = _grid_problem((13, 11, 9), 3, 4, "7pt_fv_3d", seed=1)
+    opts = Options(scheme="nest_2_2", degree=1)
+    F = factorize(A, H, opts)
+    Ad, _, ranks = dense_sgf(A, H, opts)
+    assert ranks == F.ranks()
+    assert ranks != factorize(A, H, Options(scheme="nest_2_all", degree=1)).ranks()
     Al = F.dense_operator()
     assert np.abs(Al - Ad).max() <= 1e-12 * np.abs(Ad).max()
     assert np.linalg.eigvalsh(0.5 * (Ad + Ad.T))[0] > 0
