@@ -75,9 +75,13 @@ typedef enum {
   SGF_SCHEME_NEST_ALL_ALL = 0, /* every separator cell of dimension >= 1      */
   SGF_SCHEME_NEST_2_ALL = 1,   /* codimension-1 separators only               */
   SGF_SCHEME_NONE = 2,         /* no compression: exact block Cholesky        */
-  SGF_SCHEME_GEN_ALL_ALL = 3   /* general partitions (Sec. 5.2): cells of      */
+  SGF_SCHEME_GEN_ALL_ALL = 3,  /* general partitions (Sec. 5.2): cells of      */
                                /* (b 2^(t-1))^3 vertices, no interiors, every  */
                                /* node compressed                              */
+  SGF_SCHEME_NEST_2_2 = 4      /* codimension-1 separators, their blocks to the*/
+                               /* lower-dimensional separators on their rim    */
+                               /* (boxes at most one grid step apart) kept     */
+                               /* exactly in span(Q1)                          */
 } sgf_scheme;
 
 typedef enum { SGF_BASIS_POLY = 0, SGF_BASIS_RBM = 1 } sgf_basis;

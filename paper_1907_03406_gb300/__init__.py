@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib as L
 
 STENCILS = {"5pt_2d": 0, "7pt_3d": 1, "7pt_fv_3d": 2, "q1_elastic_3d": 3}
-SCHEMES = {"nest_all_all": 0, "nest_2_all": 1, "none": 2, "gen_all_all": 3}
+SCHEMES = {"nest_all_all": 0, "nest_2_all": 1, "none": 2, "gen_all_all": 3, "nest_2_2": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 OK = 0

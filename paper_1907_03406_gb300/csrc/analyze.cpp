@@ -292,7 +292,7 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
   if (op->leaf < 2) { err = "leaf must be >= 2"; return SGF_ERR_INVALID_ARG; }
   if (op->degree < 0 || op->degree > 2) { err = "degree must be 0, 1 or 2"; return SGF_ERR_INVALID_ARG; }
   if (!elastic && op->basis != SGF_BASIS_POLY) { err = "scalar problems use the polynomial basis"; return SGF_ERR_UNSUPPORTED; }
-  if (op->scheme < 0 || op->scheme > 3) { err = "bad scheme"; return SGF_ERR_INVALID_ARG; }
+  if (op->scheme < 0 || op->scheme > 4) { err = "bad scheme"; return SGF_ERR_INVALID_ARG; }
   const bool general = op->scheme == SGF_SCHEME_GEN_ALL_ALL;
   if (op->precision != SGF_PREC_FP64 && op->precision != SGF_PREC_MIXED) { err = "bad precision"; return SGF_ERR_INVALID_ARG; }
 
@@ -420,7 +420,7 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* op, Plan& P, std::st
       bool el = false;
       if (!c.in && t >= std::max(1, op->compress_from_level)) {
         if (op->scheme == SGF_SCHEME_NEST_ALL_ALL) el = cd >= 1;
-        else if (op->scheme == SGF_SCHEME_NEST_2_ALL) el = cd == dim - 1;
+        else if (op->scheme == SGF_SCHEME_NEST_2_ALL || op->scheme == SGF_SCHEME_NEST_2_2) el = cd == dim - 1;
         else if (op->scheme == SGF_SCHEME_GEN_ALL_ALL) el = true;
       }
       L.eligible[i] = el;

@@ -1118,6 +1118,19 @@ class FactorImpl final : public FactorBase {
       // gofs[B][k]: column offset of neighbour nball[B][k] in B's gathered block
       std::vector<std::vector<int>> gofs(nn);
       std::vector<int> eidx(nn, -1);
+      // Nest-2-2: per compressed node, the neighbours (indices into nball) that
+      // are lower-dimensional separators on its rim - boxes at most one grid
+      // step apart on every axis; their whole blocks M^_BE join N
+      const bool rim = P.opts.scheme == SGF_SCHEME_NEST_2_2;
+      std::vector<std::vector<int>> adj(ne);
+      auto touching = [&](int B, int X) {
+        if (L.interior[X] || L.cell_dim[X] >= P.grid.dim - 1) return false;
+        for (int a = 0; a < 3; ++a) {
+          const int gap = std::max({0, L.box[6 * X + a] - L.box[6 * B + 3 + a], L.box[6 * B + a] - L.box[6 * X + 3 + a]});
+          if (gap > 1) return false;
+        }
+        return true;
+      };
       auto gcol = [&](int B, int N) {
         const auto& v = nball[B];
         const auto it = std::lower_bound(v.begin(), v.end(), N);
@@ -1131,6 +1144,12 @@ class FactorImpl final : public FactorBase {
         for (int N : nball[B]) { gofs[B].push_back(sB); sB += m[N]; }
         sw[e] = sB;
         cw[e] = pi * (1 + (int)nball[B].size());
+        if (rim)
+          for (size_t k = 0; k < nball[B].size(); ++k)
+            if (m[nball[B][k]] > 0 && touching(B, nball[B][k])) {
+              adj[e].push_back((int)k);
+              cw[e] += m[nball[B][k]];
+            }
         o_mm[e] = t_mm; t_mm += (int64_t)m[B] * m[B];
         o_ms[e] = t_ms; t_ms += (int64_t)m[B] * sB;
         o_mc[e] = t_mc; t_mc += (int64_t)m[B] * cw[e];
@@ -1198,6 +1217,19 @@ class FactorImpl final : public FactorBase {
           }
         }
         gl.emit(b, s);
+        if (rim) {   // the rim blocks, whole, after the polynomial columns
+          CopyList<T, T> ca;
+          for (int e = 0; e < ne; ++e) {
+            const int B = E[e], mb = m[B];
+            size_t col = (size_t)pi * (1 + nball[B].size());
+            for (int k : adj[e]) {
+              const int X = nball[B][k];
+              ca.add(Mh + o_ms[e] + (size_t)gofs[B][k] * mb, mb, Nm + o_mc[e] + col * mb, mb, mb, m[X], kCopy);
+              col += m[X];
+            }
+          }
+          ca.emit(b, s);
+        }
         b.run(s);
         CopyList<T, T> cp;
         for (int e = 0; e < ne; ++e) cp.add(Nm + o_mc[e], m[E[e]], LtP + o_mp[e], m[E[e]], m[E[e]], pi, kCopy);
@@ -1211,6 +1243,7 @@ class FactorImpl final : public FactorBase {
           const int B = E[e];
           int ce = L.act[B];
           for (int N : nball[B]) ce += L.act[N];
+          for (int k : adj[e]) ce += m[nball[B][k]];
           ce = std::min(ce, cw[e]);
           QrTask<T> q{Nm + o_mc[e], Q1 + o_mm[e], m[B], cw[e], B, e};
           const long long need = (long long)m[B] * ce;

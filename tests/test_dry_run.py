@@ -61,6 +61,9 @@ CASES = [
     [[20, 20, 20], 3, "7pt_fv_3d", 1, 5, 2, "fp64", "gen_all_all"],
     [[24, 23, 17], 3, "7pt_fv_3d", 1, 5, 2, "mixed", "gen_all_all"],
     [[23, 19, 1], 2, "5pt_2d", 15, 4, 1, "fp64", "gen_all_all"],
+    [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "mixed", "nest_2_2"],
+    [[21, 18, 13], 3, "7pt_fv_3d", 1, 4, 1, "fp64", "nest_2_2"],
+    [[41, 37, 1], 2, "5pt_2d", 15, 4, 1, "fp64", "nest_2_2"],
     [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "mixed", "nest_all_all",
      {"gemv_min_elems": 256, "gemv_max_elems": 1024, "front_small": 64, "tensor_cores": 0, "gemv_cols": 64}],
     [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "fp64", "nest_all_all",

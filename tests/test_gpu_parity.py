@@ -321,3 +321,32 @@ def test_full_size_128cube_two_phase_properties():
         F.close()
     print(f"128^3 two-phase PCG iterations: {its}")
     assert its["mixed"] <= 1.3 * its["fp64"]
+
+
+@pytest.mark.parametrize("name", ["rand2d_45_39_4", "rand3d_21_18_13_4", "grf3d_24"])
+def test_nest_2_2_matches_oracle(name):
+    # Nest-2-2 (Sec. 5.1): ranks equal, apply / multiply within the oracle's
+    # own sensitivity, PCG iterations within +-1, and the mixed path converges
+    cfg = dict(_problem(name), scheme="nest_2_2")
+    A, H, O = _oracle(cfg)
+    plan, F = _gpu(cfg)
+    assert any(v["adj_cols"] > 0 and v["compressed"] for v in O.comp_info.values())
+    for li, lev in enumerate(H.levels[:-1]):
+        m, r = F.ranks(li, lev.nnodes)
+        for node in range(lev.nnodes):
+            if (lev.t, node) in O.comp_info:
+                v = O.comp_info[(lev.t, node)]
+                assert (m[node], r[node]) == (v["m"], v["r"]), (lev.t, node)
+    v = np.random.default_rng(7).standard_normal(plan.n)
+    ta, tm = _tolerance(cfg, v)
+    yo, zo = O.solve(v), O.multiply(v)
+    assert np.linalg.norm(F.apply(_t(v)).cpu().numpy() - yo) <= ta * np.linalg.norm(yo)
+    assert np.linalg.norm(F.apply_forward(_t(v)).cpu().numpy() - zo) <= tm * np.linalg.norm(zo)
+    b = si.rhs(plan.n, 0)
+    _, it_o, _ = pcg(lambda u: A @ u, O.solve, b)
+    _, info = F.pcg(_t(b), rtol=1e-10, maxit=500)
+    assert abs(info["iterations"] - it_o) <= 1 and info["rel_residual"] <= 1e-10
+    F.close()
+    _, Fm = _gpu(cfg, precision="mixed")
+    _, info = Fm.pcg(_t(b), rtol=1e-10, maxit=500)
+    assert info["rel_residual"] <= 1e-10
