@@ -26,7 +26,8 @@ import time
 import numpy as np
 
 
-def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000, family: str = "poisson3d"):
+def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000, family: str = "poisson3d",
+        scheme: str | None = None):
     import torch
 
     import sgf_inputs as si
@@ -37,7 +38,8 @@ def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000, family: s
     rows = []
     for e in sizes:
         cfg = si.config(f"{family}_{e}")
-        plan = Plan.from_config(cfg, precision=precision)
+        kw = {"scheme": scheme} if scheme else {}
+        plan = Plan.from_config(cfg, precision=precision, **kw)
         coeffs = torch.tensor(np.ascontiguousarray(cfg["coeffs"]).ravel(), dtype=torch.float64, device=dev)
         b = torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
@@ -65,7 +67,8 @@ def run(sizes, precision: str, rtol: float = 1e-10, maxit: int = 1000, family: s
             F.apply(b)
         e1.record()
         torch.cuda.synchronize()
-        row = dict(family=family, edge=e, n=plan.n, precision=F.precision, factor_ms=round(1e3 * (t1 - t0), 1),
+        row = dict(family=family, scheme=scheme or cfg.get("scheme", "nest_all_all"), edge=e, n=plan.n,
+                   precision=F.precision, factor_ms=round(1e3 * (t1 - t0), 1),
                    first_factor_ms=round(first_ms, 1), pcg_ms=round(1e3 * (t2 - t1), 1), iterations=info["iterations"],
                    rel_residual=info["rel_residual"], apply_ms=round(e0.elapsed_time(e1) / 3, 3),
                    factor_gb=round((free0 - free1) / 1e9, 2),
@@ -83,8 +86,10 @@ def main():
     ap.add_argument("--sizes", type=int, nargs="+", default=[32, 64, 128])
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--family", choices=["poisson3d", "grf3d", "twophase3d", "elastic"], default="poisson3d")
+    ap.add_argument("--scheme", choices=["nest_all_all", "nest_2_all", "nest_2_2"], default=None,
+                    help="compression scheme (default: the workload's)")
     args = ap.parse_args()
-    run(args.sizes, args.precision, family=args.family)
+    run(args.sizes, args.precision, family=args.family, scheme=args.scheme)
 
 
 if __name__ == "__main__":
