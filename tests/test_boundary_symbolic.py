@@ -81,6 +81,21 @@ def test_symbolic_analysis_bit_exact(n, dim, b, st):
             assert not lev.interior.any()
 
 
+@pytest.mark.parametrize("scheme", ["nest_all_all", "nest_2_all", "nest_2_2", "none"])
+@pytest.mark.parametrize("n,dim,b,st", [((37, 29, 23), 3, 8, "7pt_fv_3d"), ((41, 37, 1), 2, 4, "5pt_2d")])
+def test_eligibility_per_scheme_matches_oracle(scheme, n, dim, b, st):
+    from oracle.sgf import Options, _eligible
+    H = build_hierarchy(n, dim, b, st)
+    P = sgf.Plan(n, dim, st, 1, b, 1, scheme=scheme)
+    opts = Options(scheme=scheme)
+    for li, lev in enumerate(H.levels):
+        if lev.top:
+            continue
+        ex = P.export_level(li)
+        want = [_eligible(lev, i, dim, opts) and not lev.interior[i] for i in range(lev.nnodes)]
+        assert [bool(v) for v in ex["eligible"].tolist()] == want
+
+
 def test_analyze_rejects_bad_arguments():
     with pytest.raises(sgf.SGFError):
         sgf.Plan((16, 16, 16), 3, "7pt_fv_3d", 1, 1, 2)      # leaf < 2
