@@ -94,20 +94,9 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
-            return
-        # the timed region starts only once the sampler is writing (its start-up
-        # takes longer than a short timed region)
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
-            try:
-                if os.path.getsize(self.path) > 0:
-                    break
-            except OSError:
-                pass
-            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
