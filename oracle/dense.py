@@ -16,9 +16,19 @@ the approximation after k levels is A_k = F M F^T (Sec. 2.1, Sec. 6).
   M[s[:r], others] = Q1^T M^, and the Q2 rows are decoupled (set to zero).
 * Merge: a parent's slots are its children's surviving slots.
 
+* Which nodes a scheme compresses (Sec. 5.1, Sec. 5.2) and the Nest-2-2
+  rim are decided here from the cells' geometry, independently of `sgf`:
+  the dimension of a cell is that of the affine hull of its points (the
+  number of axes along which its box is more than one point wide), the
+  interiors have full dimension; Nest-All-All compresses every separator of
+  dimension >= 1, Nest-2-All and Nest-2-2 those of codimension 1, Gen-All-All
+  every node; a lower-dimensional separator X lies on the rim of a
+  codimension-1 separator B when some point of X is within one grid step of
+  some point of B along every axis (brute force over the point pairs).
+
 This is a second, independent implementation written against the same
-equations; it shares no code with `sgf` beyond the partition and the basis
-evaluation.
+equations; it shares no code with `sgf` beyond the partition, the basis
+evaluation and the DOF numbering.
 """
 from __future__ import annotations
 
@@ -26,7 +36,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .basis import Basis
-from .sgf import Options, _eligible, adjacent_low, dof_list, point_coords
+from .sgf import Options, dof_list, point_coords
 
 
 def _cell_dofs(H, box):
@@ -37,6 +47,45 @@ def _cell_dofs(H, box):
     zz, yy, xx = np.meshgrid(zs, ys, xs, indexing="ij")
     pts = (xx + nx * (yy + ny * zz)).ravel()
     return np.sort(pts)
+
+
+def _cell_dim(H, box):
+    """Dimension of the affine hull of a cell's points."""
+    lo, hi = np.asarray(box[0]), np.asarray(box[1])
+    return int(np.sum(hi[:H.dim] > lo[:H.dim]))
+
+
+def _compressed_by_scheme(H, lev, X, opts: Options) -> bool:
+    """Sec. 5.1 / 5.2: is node X of this level selected for compression?"""
+    if opts.scheme == "none" or lev.t < opts.compress_from_level:
+        return False
+    if opts.scheme == "gen_all_all":
+        return True
+    # nested dissection: intervals are at least two points wide for b >= 3,
+    # so a cell's affine dimension is its number of interval axes
+    assert H.leaf >= 3, "geometric cell dimension needs leaf >= 3"
+    cd = _cell_dim(H, lev.box[X])
+    if cd == H.dim:
+        return False                 # an interior: eliminated, not compressed
+    if opts.scheme == "nest_all_all":
+        return cd >= 1               # 0-cells are not compressed (Sec. 5.1)
+    if opts.scheme in ("nest_2_all", "nest_2_2"):
+        return cd == H.dim - 1
+    raise ValueError(opts.scheme)
+
+
+def _on_rim(H, lev, B, X) -> bool:
+    """Nest-2-2: X is a lower-dimensional separator touching separator B."""
+    if _cell_dim(H, lev.box[X]) >= H.dim - 1:     # interiors and codimension-1 cells
+        return False
+    nx, ny, _ = H.n
+
+    def coords(box):
+        p = _cell_dofs(H, box)
+        return np.stack([p % nx, (p // nx) % ny, p // (nx * ny)], 1)
+    pb, px = coords(lev.box[B]), coords(lev.box[X])
+    cheb = np.abs(pb[:, None, :] - px[None, :, :]).max(axis=2)
+    return bool(cheb.min() <= 1)
 
 
 def dense_sgf(A, H, opts: Options = Options()):
@@ -78,7 +127,7 @@ def dense_sgf(A, H, opts: Options = Options()):
             M[np.ix_(s, rest)] = 0.0
             M[np.ix_(rest, s)] = 0.0
             del slots[I]
-        for B in [X for X in lev.separators() if _eligible(lev, X, H.dim, opts)]:
+        for B in [X for X in range(lev.nnodes) if not lev.interior[X] and _compressed_by_scheme(H, lev, X, opts)]:
             s = slots[B]
             others_nodes = [X for X in slots if X != B]
             others = [q for X in others_nodes for q in slots[X]]
@@ -91,7 +140,7 @@ def dense_sgf(A, H, opts: Options = Options()):
             for X in others_nodes:
                 k = len(slots[X])
                 cols.append(Mh[:, o:o + k] @ (FT @ Pi_of(lev, X))[slots[X]])
-                if opts.scheme == "nest_2_2" and adjacent_low(lev, B, X, H.dim):
+                if opts.scheme == "nest_2_2" and _on_rim(H, lev, B, X):
                     adj.append(Mh[:, o:o + k])   # kept exactly: whole block in span(Q1)
                 o += k
             Nmat = np.hstack(cols + adj)

@@ -346,3 +346,20 @@ def test_n22_dense_brute_force_reproduces_block_oracle():
     Al = F.dense_operator()
     assert np.abs(Al - Ad).max() <= 1e-12 * np.abs(Ad).max()
     assert np.linalg.eigvalsh(0.5 * (Ad + Ad.T))[0] > 0
+
+
+def test_P5_catches_a_scheme_selection_mistake(monkeypatch):
+    # the dense restatement selects the compressed cells on its own (from the
+    # cells' geometry); a wrong selection rule in the block oracle shows up
+    import oracle.sgf as osgf
+    A, H = _grid_problem((13, 11, 9), 3, 4, "7pt_fv_3d", seed=1)
+    opts = Options(scheme="nest_2_all", degree=1)
+    Ad, _, ranks = dense_sgf(A, H, opts)
+    assert ranks == factorize(A, H, opts).ranks()
+    good = osgf._eligible
+
+    def wrong(lev, i, dim, o):   # Nest-2-All mistaken for Nest-All-All
+        return good(lev, i, dim, Options(scheme="nest_all_all", tau=o.tau, degree=o.degree))
+    monkeypatch.setattr(osgf, "_eligible", wrong)
+    assert factorize(A, H, opts).ranks() != ranks
+
