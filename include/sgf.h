@@ -142,17 +142,26 @@ int sgf_plan_footprint(const sgf_plan* plan, size_t* bytes_fp64, size_t* bytes_m
  *     this range); 256 <= min <= max <= 1 << 20.
  *   front_small: largest front (rows) the one-CTA elimination kernel takes in
  *     a batch of at least one front per SM (single precision); 64..512.
- *   tensor_cores: 1 = single-precision factor GEMMs on the tensor cores as
- *     3xTF32 split products, 0 = FP32 CUDA cores.
+ *   tensor_cores: single-precision factor GEMMs on the tensor cores with
+ *     every FP32 operand split into TF32 parts: 1 = two parts and three
+ *     products (the 3xTF32 scheme), 2 = three parts and six products; both
+ *     flush the tensor-core partial sums to FP32 registers every 32 terms of
+ *     K (the tensor cores accumulate with truncation); 0 = FP32 CUDA cores
+ *     only.
  *   gemv_cols: outputs per apply GEMV task of the transposed (column dot
  *     product) form, 32 or 64 (single precision; double precision uses 32).
- * Defaults: 4096, 32768, 512, 1, 32.                                         */
+ *   tc_min_dim: a product goes to the tensor cores (128 x 128 tiles) only
+ *     when both dimensions of its output block are at least this, else to
+ *     64 x 64 CUDA-core tiles (small blocks would leave most of a tensor-core
+ *     tile empty); 1..4096.
+ * Defaults: 4096, 32768, 512, 1, 32, 64.                                     */
 typedef struct {
   int gemv_min_elems;
   int gemv_max_elems;
   int front_small;
   int tensor_cores;
   int gemv_cols;
+  int tc_min_dim;
 } sgf_tuning;
 
 /* Current tuning of a plan (INVALID_ARG on NULL). */
@@ -162,8 +171,9 @@ int sgf_plan_get_tuning(const sgf_plan* plan, sgf_tuning* out);
 int sgf_plan_set_tuning(sgf_plan* plan, const sgf_tuning* t);
 /* Autotuner: searches the launch shapes with CUDA events on `stream`, after
  * one untimed warm-up factorization of coeffs_dev.  First, in single
- * precision, front_small x tensor_cores (512/256 x 1/0), each timed as the
- * faster of two sgf_factor calls; then, with the fastest of those, five GEMV
+ * precision, front_small (512, 256) x tc_min_dim (32, 64, 128) with the
+ * plan's tensor-core mode (1 when it is 0), each timed as the faster of two
+ * sgf_factor calls; then, with the fastest of those, five GEMV
  * budgets (4K-32K, 8K-64K, 16K-128K, 32K-128K, 32K-256K elements per task),
  * in single precision each with gemv_cols 32 and 64, each timed on napply
  * applications of A_l^{-1} to a fixed vector (skipped
@@ -221,9 +231,11 @@ int sgf_spmv(const sgf_factor_t* f, const double* x_dev, double* y_dev, int nrhs
  * NULL) receives iterations, the true relative residual ||b - A x|| / ||b||
  * and the device time.  Returns NO_CONVERGENCE when maxit was reached.      */
 typedef struct sgf_solve_info {
-  int iterations;      /* max over right-hand sides   */
-  double rel_residual; /* max over right-hand sides   */
-  double seconds;      /* device time of the solve    */
+  int iterations;      /* max over right-hand sides                          */
+  double rel_residual; /* max over right-hand sides                          */
+  double seconds;      /* time of the solve: device time (CUDA events) for   */
+                       /* sgf_pcg_solve, host wall time for                  */
+                       /* sgf_pcg_solve_noalloc                              */
 } sgf_solve_info;
 
 int sgf_pcg_solve(const sgf_factor_t* f, const double* b_dev, double* x_dev, int nrhs,
@@ -240,13 +252,17 @@ int sgf_pcg_solve(const sgf_factor_t* f, const double* b_dev, double* x_dev, int
  * array of 5 * SGF_NOALLOC_MAX_UNKNOWNS + 368 doubles (about 10 MiB) that
  * every GPU loading the library keeps until the process exits; factors with
  * more than SGF_NOALLOC_MAX_UNKNOWNS unknowns are rejected with
- * SGF_ERR_INVALID_ARG.  It calls no allocator.  The first call on a device
- * looks up the array's device address (once per device, with that device
- * current): make that first call before any stream capture.  Every call
- * shares the one array and writes each word it reads, so nothing carries
- * over between calls, but calls that overlap on the GPU (other streams or
- * threads) race on it and must not be issued.  Synchronizes the stream;
- * info->seconds is host wall time.                                         */
+ * SGF_ERR_INVALID_ARG, and so is a call whose current device is not the
+ * factor's.  It calls no allocator: sgf_factor builds and instantiates the
+ * single-RHS apply graph this solve replays, so nothing is captured or
+ * instantiated here either (sgf_memory_stats shows no new allocation event
+ * across a call).  The first call on a device looks up the array's device
+ * address (once per device, with that device current): make that first
+ * call before any stream capture.  Every call shares the one array and
+ * writes each word it reads, so nothing carries over between calls, but
+ * calls that overlap on the GPU (other streams or threads) race on it and
+ * must not be issued.  Synchronizes the stream; info->seconds is host wall
+ * time.                                                                    */
 #define SGF_NOALLOC_MAX_UNKNOWNS 262144
 int sgf_pcg_solve_noalloc(const sgf_factor_t* f, const double* b_dev, double* x_dev, double rtol,
                           int maxit, void* stream, sgf_solve_info* info);
@@ -256,6 +272,26 @@ int sgf_pcg_solve_noalloc(const sgf_factor_t* f, const double* b_dev, double* x_
 int sgf_solve_host(const sgf_plan* plan, const double* coeffs_host, const double* b_host,
                    double* x_host, int nrhs, double rtol, int maxit, void* stream,
                    sgf_solve_info* info);
+
+/* ---- asynchronous status ---------------------------------------------------
+ * sgf_sync: waits for the current device (the factor's; INVALID_ARG when
+ * another device is current) and surfaces what the asynchronous work issued
+ * for this factor found (Sec. 4.7 applies and products are enqueued and
+ * return before the device has run them): SGF_ERR_CUDA for a sticky CUDA
+ * error, the factorization's pivot status (NOT_SPD / NONFINITE), then
+ * SGF_ERR_NONFINITE when an sgf_apply or sgf_apply_forward since the last
+ * sgf_sync wrote a NaN or infinity into its output (that flag is cleared by
+ * this call), else SGF_OK.  The check is folded into the final copy of every
+ * apply and multiply, so it costs no extra pass over the vectors.          */
+int sgf_sync(const sgf_factor_t* f);
+
+/* Device-memory accounting: *alloc_events (may be NULL) = how many times
+ * this library has asked the CUDA runtime or driver for device memory since
+ * the process started (cudaMalloc, stream-ordered allocations, stream
+ * creation and graph instantiation each count one); *pool_used_bytes (may be
+ * NULL) = bytes in use from the current device's default stream-ordered pool
+ * (every user of that pool counted).  Host only, no synchronization.       */
+int sgf_memory_stats(int64_t* alloc_events, int64_t* pool_used_bytes);
 
 const char* sgf_status_string(int status);
 /* Human-readable message of the last failed call on the calling thread.   */

@@ -197,6 +197,12 @@ class Factor:
         return out, dict(iterations=info.iterations, rel_residual=info.rel_residual,
                          seconds=info.seconds, status=rc)
 
+    def sync(self) -> int:
+        """sgf_sync: wait for the device and return the factor's asynchronous
+        status (0, or a negative status such as -3 for a non-finite value an
+        apply produced since the last call)."""
+        return self._lib.sgf_sync(self.handle)
+
     def level_stats(self, level: int):
         nc = C.c_int()
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
@@ -234,6 +240,14 @@ def solve_host(plan: Plan, coeffs: np.ndarray, b: np.ndarray, rtol=1e-10, maxit=
                             _stream_ptr(stream), C.byref(info))
     _check(rc, "sgf_solve_host")
     return x, dict(iterations=info.iterations, rel_residual=info.rel_residual, seconds=info.seconds)
+
+
+def memory_stats() -> dict:
+    """sgf_memory_stats: the library's device allocation events so far and the
+    bytes in use from the current device's default stream-ordered pool."""
+    a, u = C.c_int64(), C.c_int64()
+    _check(L.load().sgf_memory_stats(C.byref(a), C.byref(u)), "sgf_memory_stats")
+    return dict(alloc_events=a.value, pool_used_bytes=u.value)
 
 
 def profile_reset(timing=False):

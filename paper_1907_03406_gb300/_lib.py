@@ -18,7 +18,7 @@ class sgf_grid(C.Structure):
 
 class sgf_tuning(C.Structure):
     _fields_ = [("gemv_min_elems", C.c_int), ("gemv_max_elems", C.c_int), ("front_small", C.c_int),
-                ("tensor_cores", C.c_int), ("gemv_cols", C.c_int)]
+                ("tensor_cores", C.c_int), ("gemv_cols", C.c_int), ("tc_min_dim", C.c_int)]
 
 
 class sgf_opts(C.Structure):
@@ -67,6 +67,8 @@ SIGNATURES = {
     "sgf_profile_read": (_I, [_I, _I64P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sgf_profile_kind_name": (C.c_char_p, [_I]),
     "sgf_release_cached_memory": (_I, []),
+    "sgf_sync": (_I, [_P]),
+    "sgf_memory_stats": (_I, [_I64P, _I64P]),
 }
 
 _lib = None

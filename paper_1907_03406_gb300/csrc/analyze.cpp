@@ -214,8 +214,8 @@ void q1_element_stiffness(double nu, std::vector<double>& K) {
 bool tuning_valid(const sgf_tuning& t) {
   // front_small: at most the one-CTA front kernel's limit (512 rows)
   return t.gemv_min_elems >= 256 && t.gemv_min_elems <= t.gemv_max_elems && t.gemv_max_elems <= (1 << 20) &&
-         t.front_small >= 64 && t.front_small <= 512 && (t.tensor_cores == 0 || t.tensor_cores == 1) &&
-         (t.gemv_cols == 32 || t.gemv_cols == 64);
+         t.front_small >= 64 && t.front_small <= 512 && t.tensor_cores >= 0 && t.tensor_cores <= 2 &&
+         (t.gemv_cols == 32 || t.gemv_cols == 64) && t.tc_min_dim >= 1 && t.tc_min_dim <= 4096;
 }
 
 int LevelLayout::col_of(int u, int v) const {

@@ -175,18 +175,20 @@ int sgf_autotune(sgf_plan* plan, const double* coeffs_dev, void* stream, int nap
     sgf_tuning cur = saved;
     double t_factor = 0;
     {
-      std::vector<std::pair<int, int>> shapes;   // (front_small, tensor_cores)
+      struct Shape { int fs, tc, tcmin; };
+      std::vector<Shape> shapes;
       if (mixed) {
-        for (int tc : {1, 0})
-          for (int fs : {512, 256}) shapes.push_back({fs, tc});
+        for (int fs : {512, 256})
+          for (int tcmin : {32, 64, 128}) shapes.push_back({fs, saved.tensor_cores ? saved.tensor_cores : 1, tcmin});
       } else {
-        shapes.push_back({saved.front_small, saved.tensor_cores});
+        shapes.push_back({saved.front_small, saved.tensor_cores, saved.tc_min_dim});
       }
       double bt = 1e300;
       for (const auto& sh : shapes) {
         plan->p.tune = saved;
-        plan->p.tune.front_small = sh.first;
-        plan->p.tune.tensor_cores = sh.second;
+        plan->p.tune.front_small = sh.fs;
+        plan->p.tune.tensor_cores = sh.tc;
+        plan->p.tune.tc_min_dim = sh.tcmin;
         double t = 1e300;
         for (int rep = 0; rep < 2; ++rep) {
           SGF_CK(cudaEventRecord(e0, s));
@@ -405,6 +407,36 @@ int sgf_profile_read(int kind, int64_t* launches, double* ms, double* flops, dou
   return SGF_OK;
 }
 const char* sgf_profile_kind_name(int kind) { return sgf::prof_name(kind); }
+
+int sgf_sync(const sgf_factor_t* f) {
+  if (!f) return SGF_ERR_INVALID_ARG;
+  return guarded([&] {
+    if (sgf::dry_run()) return (int)SGF_OK;
+    int cur = -1;
+    SGF_CK(cudaGetDevice(&cur));
+    if (cur != f->f->device) throw sgf::SgfError(SGF_ERR_INVALID_ARG, "factor lives on another device");
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) throw sgf::SgfError(SGF_ERR_CUDA, std::string("device: ") + cudaGetErrorString(e));
+    return f->f->device_status();
+  });
+}
+
+int sgf_memory_stats(int64_t* alloc_events, int64_t* pool_used_bytes) {
+  if (alloc_events) *alloc_events = sgf::alloc_events();
+  if (pool_used_bytes) {
+    *pool_used_bytes = 0;
+    if (!sgf::dry_run()) {
+      int dev = 0;
+      cudaMemPool_t pool;
+      uint64_t used = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
+          cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+        return SGF_ERR_CUDA;
+      *pool_used_bytes = (int64_t)used;
+    }
+  }
+  return SGF_OK;
+}
 
 int sgf_release_cached_memory(void) {
   if (!sgf::dry_run() && cudaDeviceSynchronize() != cudaSuccess) return SGF_ERR_CUDA;

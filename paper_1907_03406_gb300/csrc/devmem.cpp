@@ -1,6 +1,7 @@
 // Device memory helpers and the dry-run validator (see devmem.h).
 #include "devmem.h"
 
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -54,9 +55,14 @@ static void fake_free(void* p) {
   if (p) r.live.erase((uintptr_t)p);
 }
 
+static std::atomic<int64_t> g_alloc_events{0};
+void note_alloc_event() { g_alloc_events.fetch_add(1, std::memory_order_relaxed); }
+int64_t alloc_events() { return g_alloc_events.load(std::memory_order_relaxed); }
+
 void* dev_malloc(size_t bytes) {
   if (dry_run()) return fake_alloc(bytes);
   void* p = nullptr;
+  note_alloc_event();
   SGF_CK(cudaMalloc(&p, bytes));
   return p;
 }
@@ -85,6 +91,7 @@ void* dev_malloc_async(size_t bytes, cudaStream_t s) {
     }
   }
   void* p = nullptr;
+  note_alloc_event();
   cudaError_t e = cudaMallocAsync(&p, bytes, s);
   if (e == cudaErrorMemoryAllocation) {
     // the pool may be holding freed blocks of earlier factorizations: hand

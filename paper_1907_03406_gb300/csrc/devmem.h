@@ -26,6 +26,11 @@ void* dev_malloc_async(size_t bytes, cudaStream_t s);
 void dev_free_async(void* p, cudaStream_t s);
 // return the pool's unused cached blocks to the device
 void dev_release_cached();
+// Allocation events: every call of this library that asks the CUDA runtime
+// or driver for device memory (cudaMalloc, cudaMallocAsync, stream creation,
+// graph instantiation) adds one.
+void note_alloc_event();
+int64_t alloc_events();
 void dev_memset(void* p, int v, size_t bytes, cudaStream_t s);
 void dev_h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
 void dev_d2h(void* dst, const void* src, size_t bytes, cudaStream_t s);  // synchronous

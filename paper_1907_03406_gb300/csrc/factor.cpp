@@ -181,6 +181,15 @@ void Batch::release(cudaStream_t s) {
 
 namespace {
 
+// apply programs replayed as CUDA graphs unless SGF_APPLY_GRAPH=0
+bool apply_graph() {
+  static const bool on = [] {
+    const char* e = std::getenv("SGF_APPLY_GRAPH");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 // Launch shapes of the factorization or program build running on this thread
 // (the plan's sgf_tuning), set for its duration by TuneScope.
 thread_local const sgf_tuning* t_tune = nullptr;
@@ -190,7 +199,7 @@ struct TuneScope {
   ~TuneScope() { t_tune = prev; }
 };
 inline const sgf_tuning& active_tuning() {
-  static const sgf_tuning def{4096, 32768, 512, 1, 32};
+  static const sgf_tuning def{4096, 32768, 512, 1, 32, 64};
   return t_tune ? *t_tune : def;
 }
 
@@ -239,13 +248,18 @@ struct Spec {
 
 template <typename T>
 struct GemmList {
-  Pooled<std::vector<GemmTask<T>>> tp;
+  Pooled<std::vector<GemmTask<T>>> tp, sp;
   Pooled<std::vector<GemmContrib<T>>> cp;
-  std::vector<GemmTask<T>>& t = tp.v;
+  std::vector<GemmTask<T>>& t = tp.v;    // tensor-core tiles (kTileTC x kTileTC)
+  std::vector<GemmTask<T>>& ts = sp.v;   // CUDA-core tiles (kTile x kTile)
   std::vector<GemmContrib<T>>& c = cp.v;
-  // FP32 products go to the tensor cores (3xTF32) in kTileTC-row tiles
-  const bool tc = std::is_same<T, float>::value && gemm_tc_enabled() && active_tuning().tensor_cores;
-  const int tm = tc ? kTileTC : kTile;
+  // FP32 products of blocks with both dimensions >= tc_min_dim go to the
+  // tensor cores as split TF32 products (tensor_cores: 2 = six products,
+  // FP32-accurate; 1 = three, the 3xTF32 scheme); the rest, and all of FP64,
+  // to the CUDA cores
+  const int tcmode = std::is_same<T, float>::value && gemm_tc_enabled() ? active_tuning().tensor_cores : 0;
+  const int tcmin = active_tuning().tc_min_dim;
+  bool use_tc(int M, int N) const { return tcmode != 0 && M >= tcmin && N >= tcmin; }
   void add(T* C, int ldc, int M, int N, T alpha, int beta, std::initializer_list<Spec<T>> specs) {
     add_range(C, ldc, M, N, alpha, beta, specs.begin(), specs.end());
   }
@@ -254,13 +268,16 @@ struct GemmList {
   }
   void add_range(T* C, int ldc, int M, int N, T alpha, int beta, const Spec<T>* sb, const Spec<T>* se) {
     if (M <= 0 || N <= 0) return;
-    for (int j0 = 0; j0 < N; j0 += kTile)
+    const bool tc = use_tc(M, N);
+    const int tm = tc ? kTileTC : kTile, tn = tc ? kTileTC : kTile;
+    std::vector<GemmTask<T>>& dst = tc ? t : ts;
+    for (int j0 = 0; j0 < N; j0 += tn)
       for (int i0 = 0; i0 < M; i0 += tm) {
         GemmTask<T> g;
         g.C = C + i0 + (size_t)j0 * ldc;
         g.ldc = ldc;
         g.M = std::min(tm, M - i0);
-        g.N = std::min(kTile, N - j0);
+        g.N = std::min(tn, N - j0);
         g.c_begin = (int)c.size();
         g.alpha = alpha;
         g.beta = beta;
@@ -279,7 +296,7 @@ struct GemmList {
           ++cnt;
         }
         g.c_count = cnt;
-        t.push_back(g);
+        dst.push_back(g);
       }
   }
   // tasks of another list, after this list's (contribution indices shifted)
@@ -290,39 +307,58 @@ struct GemmList {
       g.c_begin += base;
       t.push_back(g);
     }
+    ts.reserve(ts.size() + o.ts.size());
+    for (GemmTask<T> g : o.ts) {
+      g.c_begin += base;
+      ts.push_back(g);
+    }
     c.insert(c.end(), o.c.begin(), o.c.end());
   }
-  // C[M x N] = Li B with Li lower triangular (M x M): row tile i0 needs only
-  // the first min(M, i0 + 64) rows of B
+  // C[M x N] = Li B with Li lower triangular (M x M): a row band starting at
+  // i0 needs only the first min(M, i0 + band) rows of B
   void add_lowtri(T* C, int ldc, int M, int N, const T* Li, int ldli, const T* B, int ldb) {
+    const int tm = use_tc(M, N) ? kTileTC : kTile;
     for (int i0 = 0; i0 < M; i0 += tm) {
       const int K = std::min(M, i0 + tm);
       add(C + i0, ldc, std::min(tm, M - i0), N, T(1), 0, {{Li + i0, ldli, false, B, ldb, false, K}});
     }
   }
-  void emit(Batch& b, cudaStream_t s) {
-    if (t.empty()) return;
-    double fl = 0, by = 0;
-    for (const auto& g : t)
+  static void work(const std::vector<GemmTask<T>>& v, const std::vector<GemmContrib<T>>& c, double& fl, double& by) {
+    fl = by = 0;
+    for (const auto& g : v) {
       for (int k = g.c_begin; k < g.c_begin + g.c_count; ++k) {
         fl += 2.0 * g.M * g.N * c[k].K;
         by += (double)sizeof(T) * ((double)g.M * c[k].K + (double)c[k].K * g.N);
       }
-    for (const auto& g : t) by += (double)sizeof(T) * g.M * g.N * (g.beta ? 2 : 1);
-    const size_t ot = b.push(t), oc = b.push(c);
-    const int n = (int)t.size();
-    const bool use_tc = tc;
-    b.launches.push_back([=](const char* d) {
-      prof_work(fl, by);
-      if constexpr (std::is_same<T, float>::value) {
-        if (use_tc) {
-          launch_gemm_tc((const GemmTask<float>*)(d + ot), (const GemmContrib<float>*)(d + oc), n, s);
-          return;
-        }
-      }
-      launch_gemm<T>((const GemmTask<T>*)(d + ot), (const GemmContrib<T>*)(d + oc), n, s);
-    });
+      by += (double)sizeof(T) * g.M * g.N * (g.beta ? 2 : 1);
+    }
+  }
+  void emit(Batch& b, cudaStream_t s) {
+    if (t.empty() && ts.empty()) return;
+    const size_t oc = b.push(c);
+    if (!t.empty()) {
+      double fl, by;
+      work(t, c, fl, by);
+      const size_t ot = b.push(t);
+      const int n = (int)t.size(), parts = tcmode == 1 ? 2 : 3;
+      b.launches.push_back([=](const char* d) {
+        prof_work(fl, by);
+        if constexpr (std::is_same<T, float>::value)
+          launch_gemm_tc((const GemmTask<float>*)(d + ot), (const GemmContrib<float>*)(d + oc), n, parts, s);
+      });
+    }
+    if (!ts.empty()) {
+      double fl, by;
+      work(ts, c, fl, by);
+      const size_t ot = b.push(ts);
+      const int n = (int)ts.size();
+      b.launches.push_back([=](const char* d) {
+        prof_work(fl, by);
+        launch_gemm<T>((const GemmTask<T>*)(d + ot), (const GemmContrib<T>*)(d + oc), n, s);
+      });
+    }
     t.clear();
+    ts.clear();
     c.clear();
   }
 };
@@ -387,7 +423,8 @@ struct Front {
 // Blocked right-looking Cholesky of D with the triangular solves of the panel
 // and of the identity (giving L^{-1}), batched over all fronts.
 template <typename T>
-void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level) {
+void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level,
+                std::vector<void*>& work) {
   // Small fronts without a panel: one CTA does the whole sweep.  Beyond
   // front_small the tile sweep spread over many CTAs wins (one CTA pays a
   // memory latency per tile product), and so it does for fronts above
@@ -397,11 +434,35 @@ void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, Dev
   for (const auto& f : Fall)
     if (f.s == 0 && f.m <= small_max) ++nfit;
   const int cut = nfit >= kFrontBatchMin ? small_max : std::min(kFrontTiny, small_max);
+  // single precision: every front's diagonal before elimination, for the
+  // pivot-significance check (kPivotLoss)
+  std::vector<const T*> d0(Fall.size(), nullptr);
+  if (std::is_same<T, float>::value && !Fall.empty()) {
+    size_t tot = 0;
+    for (const auto& f : Fall) tot += f.m;
+    T* dsave = (T*)dev_malloc_async(sizeof(T) * std::max<size_t>(tot, 1), s);
+    work.push_back(dsave);
+    CopyList<T, T> cd;
+    size_t o = 0;
+    for (size_t k = 0; k < Fall.size(); ++k) {
+      const auto& f = Fall[k];
+      if (f.m > 0) cd.add(f.D, f.m + 1, dsave + o, 1, 1, f.m, kCopy);   // the diagonal: stride m + 1
+      d0[k] = dsave + o;
+      o += f.m;
+    }
+    cd.emit(b, s);
+  }
   std::vector<FrontTask<T>> small;
   std::vector<Front<T>> F;
-  for (const auto& f : Fall) {
-    if (f.s == 0 && f.m <= cut) small.push_back({f.D, f.Li, f.m, f.node});
-    else F.push_back(f);
+  std::vector<const T*> Fd0;
+  for (size_t k = 0; k < Fall.size(); ++k) {
+    const auto& f = Fall[k];
+    if (f.s == 0 && f.m <= cut) {
+      small.push_back({f.D, f.Li, d0[k], f.m, f.node});
+    } else {
+      F.push_back(f);
+      Fd0.push_back(d0[k]);
+    }
   }
   if (!small.empty()) {
     const size_t of = b.push(small);
@@ -418,13 +479,14 @@ void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, Dev
   for (int k = 0; k < kmax; ++k) {
     std::vector<DiagTask<T>> dt;
     GemmList<T> panel, update;
-    for (const auto& f : F) {
+    for (size_t fi = 0; fi < F.size(); ++fi) {
+      const auto& f = F[fi];
       const int m = f.m, nt = (m + kTile - 1) / kTile;
       if (k >= nt) continue;
       const int r0 = k * kTile, nk = std::min(kTile, m - r0), r1 = r0 + nk;
       T* Dkk = f.D + r0 + (size_t)r0 * m;
       T* Likk = f.Li + r0 + (size_t)r0 * m;
-      dt.push_back({Dkk, Likk, m, m, nk, f.node});
+      dt.push_back({Dkk, Likk, Fd0[fi] ? Fd0[fi] + r0 : nullptr, m, m, nk, f.node});
       // panel: L_ik = A_ik L_kk^{-T} (i > k); X_k = L_kk^{-1} B_k for the RHS
       for (int ri = r1; ri < m; ri += kTile) {
         const int ni = std::min(kTile, m - ri);
@@ -603,7 +665,9 @@ struct GemvList {
     npart = 0;
     ncnt = 0;
     std::vector<int> pre;
-    for (const GemvTask<T>& g : t) {
+    std::vector<GemvTask<T>> pcs;
+    for (size_t gi = 0; gi < t.size(); ++gi) {
+      const GemvTask<T>& g = t[gi];
       pre.assign(1, 0);
       for (int k = 0; k < g.c_count; ++k) {
         const GemvContrib<T>& q = c[g.c_begin + k];
@@ -621,12 +685,12 @@ struct GemvList {
       }
       const int span = std::max(1, (int)(budget / g.M));
       const int npieces = std::max(1, (total + span - 1) / span);
-      if (npieces == 1 && g.c_count <= kGemvMaxC) {
+      if (npieces == 1 && g.c_count <= kGemvMaxC) {   // unsplit
         out.push_back(g);
         continue;
       }
+      pcs.clear();
       const int len = (total + npieces - 1) / npieces;
-      const size_t first = out.size();
       int cf = 0;
       for (int a = 0; a < total;) {
         while (pre[cf + 1] <= a) ++cf;
@@ -638,17 +702,18 @@ struct GemvList {
         h.c_count = cl - cf + 1;
         h.k_lo = a - pre[cf];
         h.k_hi = b - pre[cf];
-        out.push_back(h);
+        pcs.push_back(h);
         a = b;
       }
-      const int ns = (int)(out.size() - first);
+      const int ns = (int)pcs.size();
       for (int k = 0; k < ns; ++k) {
-        GemvTask<T>& h = out[first + k];
+        GemvTask<T> h = pcs[k];
         h.split = k;
         h.nsplit = ns;
         // offsets for now; made pointers once the buffers exist
         h.part = (T*)(uintptr_t)(npart * sizeof(T));
         h.cnt = (int*)(uintptr_t)((size_t)ncnt * sizeof(int));
+        out.push_back(h);
       }
       if (ns > 1) {
         npart += (size_t)ns * g.M * nr;
@@ -700,17 +765,31 @@ struct GemvList {
         h.cnt = nullptr;
       }
     }
-    const size_t ot = P.b.push(tasks), oc = P.b.push(c);
-    const int n = (int)tasks.size();
+    // chunks too small to fill a CTA are run one per warp (eight to a block,
+    // largest first) in the same launch; split and large chunks keep a CTA each
+    std::vector<GemvTask<T>> wt, ct;
+    for (const GemvTask<T>& h : tasks) {
+      const double el = (double)h.M * (h.k_hi - h.k_lo);
+      if (h.nsplit == 1 && el <= kGemvWarpElems && (trans || h.M <= kGemvWarpRowsMax)) wt.push_back(h);
+      else ct.push_back(h);
+    }
+    std::stable_sort(wt.begin(), wt.end(), [](const GemvTask<T>& a, const GemvTask<T>& b) {
+      return (double)a.M * (a.k_hi - a.k_lo) > (double)b.M * (b.k_hi - b.k_lo);
+    });
+    const size_t oc = P.b.push(c);
+    const size_t ot = ct.empty() ? 0 : P.b.push(ct), ow = wt.empty() ? 0 : P.b.push(wt);
+    const int n = (int)ct.size(), nw = (int)wt.size();
     const bool tr = trans;
     const int r = nr, cw = cols;
     int max_m = 1;
-    for (const auto& h : tasks) max_m = std::max(max_m, h.M);
+    for (const auto& h : ct) max_m = std::max(max_m, h.M);
     P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl * r, by});
     P.ops.push_back([=](const char* d, cudaStream_t st) {
       prof_work(fl * r, by);
-      if (tr) launch_gemv_t<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, cw, st);
-      else launch_gemv_n<T>((const GemvTask<T>*)(d + ot), (const GemvContrib<T>*)(d + oc), n, r, max_m, st);
+      const GemvTask<T>* cta = (const GemvTask<T>*)(d + ot);
+      const GemvTask<T>* wtk = nw > 0 ? (const GemvTask<T>*)(d + ow) : nullptr;
+      if (tr) launch_gemv_t<T>(cta, (const GemvContrib<T>*)(d + oc), n, r, cw, st, wtk, nw);
+      else launch_gemv_n<T>(cta, (const GemvContrib<T>*)(d + oc), n, r, max_m, st, wtk, nw);
     });
     t.clear();
     c.clear();
@@ -734,6 +813,7 @@ class FactorImpl final : public FactorBase {
     plan = &P;
     n = P.n;
     tune_ = P.tune;   // a factor keeps the launch shapes it was made with
+    if (!dry_run()) SGF_CK(cudaGetDevice(&device));
     st_ = (DevStatus*)dev_malloc_async(sizeof(DevStatus), s);
     dev_memset(st_, 0, sizeof(DevStatus), s);
     try {
@@ -746,6 +826,18 @@ class FactorImpl final : public FactorBase {
   }
   ~FactorImpl() override { release(); }
   bool mixed() const override { return sizeof(T) == 4; }
+
+  int device_status() override {
+    if (dry_run()) return SGF_OK;
+    DevStatus h;
+    SGF_CK(cudaMemcpy(&h, st_, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.code) return h.code;
+    if (h.nonfinite) {
+      SGF_CK(cudaMemset(&st_->nonfinite, 0, sizeof(int)));
+      return SGF_ERR_NONFINITE;
+    }
+    return SGF_OK;
+  }
 
   void apply(const double* x, double* y, cudaStream_t s) override { apply_n(x, y, 1, s); }
   void multiply(const double* x, double* y, cudaStream_t s) override { multiply_n(x, y, 1, s); }
@@ -822,7 +914,9 @@ class FactorImpl final : public FactorBase {
   void run_program(Program<T>& P, int nr, const double* x, double* y, int nrhs, cudaStream_t s) {
     T* v1 = lev_.empty() ? vtop_ : vb_[0];
     launch_gather<T>(x, perm1_, v1, n, nrhs, nr, s);
-    if (dry_run()) {
+    if (dry_run() || !apply_graph()) {
+      // SGF_APPLY_GRAPH=0: the program's launches issued one by one (each
+      // counted and, with profiling, timed on its own)
       for (auto& op : P.ops) op(P.b.dev, s);
     } else {
       if (!P.exec) capture(P);
@@ -838,12 +932,13 @@ class FactorImpl final : public FactorBase {
         SGF_CK(cudaGraphLaunch(P.exec, s));
       }
     }
-    launch_scatter<T>(v1, perm1_, y, n, nrhs, nr, s);
+    launch_scatter<T>(v1, perm1_, y, n, nrhs, nr, s, &st_->nonfinite);
   }
 
   // record the program's launches once on a private stream
   void capture(Program<T>& P) {
     cudaStream_t cs;
+    note_alloc_event();
     SGF_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     prof_capture(true);
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -860,6 +955,7 @@ class FactorImpl final : public FactorBase {
     prof_capture(false);
     cudaStreamDestroy(cs);
     SGF_CK(e);
+    note_alloc_event();
     SGF_CK(cudaGraphInstantiate(&P.exec, P.graph, 0));
   }
 
@@ -983,7 +1079,7 @@ class FactorImpl final : public FactorBase {
         Ltop_ = Dg;
         Litop_ = dalloc<T>(keep_, (size_t)mtop_ * mtop_, s);
         std::vector<Front<T>> F = {{Dg, mtop_, nullptr, 0, Litop_, 0}};
-        if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl);
+        if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl, work_);
         b.run(s);
         if (mtop_ > 0) {   // stream ordered after the top factor
           CopyList<T, T> cm;
@@ -1000,6 +1096,7 @@ class FactorImpl final : public FactorBase {
         ls.bytes = (int64_t)2 * mtop_ * mtop_ * sizeof(T);
         stats.push_back(ls);
         for (void* p : phiw) dev_free_async(p, s);
+        free_work(s);
         break;
       }
       LevelRec<T> rec;
@@ -1031,7 +1128,7 @@ class FactorImpl final : public FactorBase {
         for (int k = lay.up_ptr[i]; k < lay.up_ptr[i + 1]; ++k) r.nb.push_back({lay.up_nb[k], lay.up_col[k]});
         rec.in.push_back(r);
       }
-      run_fronts<T>(F, b, s, st_, lvl);
+      run_fronts<T>(F, b, s, st_, lvl, work_);
       b.run(s);
       trace(s, lvl, "interior fronts");
       {
@@ -1190,7 +1287,7 @@ class FactorImpl final : public FactorBase {
       {
         std::vector<Front<T>> FB;
         for (int e = 0; e < ne; ++e) FB.push_back({Dw + o_mm[e], m[E[e]], nullptr, 0, LiB + o_mm[e], E[e]});
-        run_fronts<T>(FB, b, s, st_, lvl);
+        run_fronts<T>(FB, b, s, st_, lvl, work_);
         {
           // M^_B,nbrs = L_B^{-1} A_B,nbrs (Eq. (compr-scale))
           GemmList<T> gm;
@@ -1499,7 +1596,11 @@ class FactorImpl final : public FactorBase {
     const int nl = (int)lev_.size();
     for (int t = 0; t < nl; ++t) ensure_vb(t, lev_[t].lay.vec_size, s);
     vtop_ = dalloc<T>(keep_, 2 * (size_t)kMaxNr * std::max(mtop_, 1), s);
-    program(true, 1, s);   // the forward (multiply) programs are built on first use
+    // the single-RHS inverse program is built and instantiated as a graph
+    // here, so that applying the factor later allocates nothing (the other
+    // programs are built on first use)
+    Program<T>& P = program(true, 1, s);
+    if (!dry_run() && apply_graph() && !P.exec) capture(P);
   }
 
   Program<T>& program(bool inverse, int nr, cudaStream_t s) {
@@ -1804,6 +1905,9 @@ int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double 
   auto dot = [&](const double* a, const double* bb, int slot) { launch_dot_n(a, bb, n, k, part, sc + 8 * slot, s); };
   auto read = [&](int nslots) { dev_d2h(h, sc, sizeof(double) * 8 * nslots, s); };   // synchronizes
   const bool flex = F.mixed();
+  // SGF_PCG_LOG=1: the recursive relative residual of the first right-hand
+  // side after every iteration, to stderr
+  static const bool plog = std::getenv("SGF_PCG_LOG") != nullptr;
   std::vector<double> bnorm(k), rz(k);
   std::vector<char> active(k);
   dev_memset(x, 0, kn * sizeof(double), s);
@@ -1846,6 +1950,7 @@ int pcg_solve_block(FactorBase& F, const double* b, double* x, int nrhs, double 
     dot(r, z, 1);
     if (flex) dot(z, ro, 2);
     read(7);
+    if (plog && bnorm[0] > 0) std::fprintf(stderr, "[sgf pcg] %d %.6e\n", it, std::sqrt(h[0]) / bnorm[0]);
     Coef8 be{};
     for (int j = 0; j < k; ++j) {
       if (!active[j]) continue;

@@ -84,7 +84,13 @@ class FactorBase {
   virtual void multiply_n(const double* x, double* y, int nrhs, cudaStream_t s) = 0;
   virtual void spmv(const double* x, double* y, cudaStream_t s) = 0;       // A
   virtual bool mixed() const = 0;
+  // Asynchronous status of the work issued for this factor so far: the
+  // device pivot status, then a non-finite value written by an apply or a
+  // multiply since the last call (that flag is cleared).  The caller has
+  // synchronized the device.
+  virtual int device_status() = 0;
   const Plan* plan = nullptr;
+  int device = -1;              // the CUDA device the factor lives on
   std::vector<LevelStats> stats;
   int bad_level = -1, bad_node = -1, status = 0;
   bool fp64_fallback = false;   // mixed request factored in FP64 (see make_factor)

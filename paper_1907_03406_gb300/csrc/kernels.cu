@@ -18,9 +18,11 @@
 // the PCG loop (Sec. 7).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstdio>
+#include <vector>
 
 #include "devmem.h"
 #include "kernels.h"
@@ -213,40 +215,46 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 }
 
 // ---------------------------------------------------------------------------
-// tensor-core tile GEMM (FP32 in, 3xTF32 products, FP32 accumulation)
+// tensor-core tile GEMM (FP32 operands as split TF32 products, FP32 accumulation)
 // ---------------------------------------------------------------------------
-// One CTA per kTileTC x kTile output tile; the contributions' K ranges are
-// walked in chunks of kTcKC.  Pipeline per chunk:
-//  1. raw FP32 chunks of op(A) (rows i) and op(B)^T (rows j) are copied into a
-//     ring of kTcStages shared-memory stages by per-thread 4-byte cp.async,
-//     kTcStages - 1 chunks ahead of the arithmetic;
-//  2. once a stage has landed, the threads split it into TF32 high parts
-//     (round to nearest) and FP32 remainders, written K-major in the
-//     no-swizzle canonical layout (core matrices of 8 rows x 16 bytes, along K
-//     128 bytes apart, along rows kTcKC / 4 * 128 bytes apart) into one of two
-//     operand buffers;
-//  3. one thread issues, per 8-wide K step, a_hi b_hi, a_hi b_lo and a_lo b_hi
-//     (tcgen05.mma kind::tf32, M = 128, N = 64) into a 64-column
-//     tensor-memory accumulator and commits them to the buffer's mbarrier, so
-//     the products of chunk i overlap the split of chunk i + 1 and the copies
-//     of the chunks after it.
-// Rows of a buffer beyond the task's M / N hold stale data (they only feed
-// accumulator rows / columns that are never read); K positions beyond a
-// contribution's K are written as zeros.  The epilogue reads the accumulator
-// with tcgen05.ld (warp w: lanes 32 (w mod 4) .. +31, columns 32 (w / 4) ..
-// +31).  Every mbarrier wait is bounded; a wait that gives up poisons the tile
-// with NaN (reported downstream as a non-finite factor) instead of hanging,
-// and the tensor memory is released on every path.
+// One CTA per kTileTC x kTileTC output tile (M, N <= 128); the contributions'
+// K ranges are walked in chunks of kTcKC.  Nine warps, specialized, with no
+// CTA barrier in the main loop:
+//  * warps 0-3 (producers) load their share of chunk c + 2 from global memory
+//    into registers, then split the values of chunk c (loaded two chunks
+//    earlier) into NPART TF32 parts (each rounded to nearest: v = p0 + p1
+//    [+ p2] up to the last part's rounding) and store them K-major in the
+//    no-swizzle canonical layout (core matrices of 8 rows x 16 bytes, 128
+//    bytes apart along K, kTcKC / 4 * 128 bytes apart along rows) into stage
+//    c mod kTcStages, then arrive on the stage's "full" mbarrier;
+//  * one thread of warp 4 waits for "full", issues per 8-wide K step the
+//    split products (NPART = 2: p0q0 + p0q1 + p1q0, the 3xTF32 scheme;
+//    NPART = 3: also p0q2 + p1q1 + p2q0) as tcgen05.mma kind::tf32 (M = N =
+//    128) and commits to the stage's "empty" mbarrier so the producers refill
+//    it.  The tensor cores accumulate with truncation, whose error grows
+//    linearly with the number of additions, so a partial sum only covers
+//    kTcFlush chunks: groups of chunks alternate between two 128-column
+//    tensor-memory accumulators ("acc full" commits, "acc empty" arrivals);
+//  * warps 5-8 (accumulators, tensor-memory lane quadrants 1, 2, 3, 0) read
+//    every finished partial with tcgen05.ld and add it to FP32 registers
+//    (round to nearest), then write C = beta C + alpha sum.
+// Rows of an operand beyond the task's M / N and K positions beyond a
+// contribution's K are stored as zeros.  Every mbarrier wait is bounded; a
+// wait that gives up stops the pipeline, waits (bounded) for the products in
+// flight, poisons the tile with NaN (reported downstream as a non-finite
+// factor) instead of hanging, and the tensor memory is released on every path.
 constexpr int kTcKC = 16;
 constexpr int kTcStages = 4;
-// raw stage: rawA[k][kTcAP] (rows i fastest), rawB[k][kTcBP]; the pitches
-// (multiples of 8 plus 8) make the split's core-matrix reads conflict-free
-constexpr int kTcAP = kTileTC + 8, kTcBP = kTile + 8;
-constexpr int kTcARaw = kTcKC * kTcAP, kTcBRaw = kTcKC * kTcBP;
-constexpr int kTcStage = kTcARaw + kTcBRaw;
-constexpr int kTcAOp = kTileTC * kTcKC, kTcBOp = kTile * kTcKC;   // canonical operand buffers
-constexpr int kTcOp = 2 * (kTcAOp + kTcBOp);                      // hi + lo of A and B
-constexpr size_t kTcSmem = sizeof(float) * ((size_t)kTcStages * kTcStage + 2 * kTcOp);
+constexpr int kTcFlush = 2;                  // chunks per tensor-memory partial sum
+constexpr int kTcThreads = 9 * 32;
+constexpr int kTcPartA = kTileTC * kTcKC;    // floats of one operand part per stage
+constexpr int kTcWaitIters = 1 << 22;
+
+template <int NPART>
+struct TcCfg {
+  static constexpr int kStage = 2 * NPART * kTcPartA;   // A and B parts
+  static constexpr size_t kSmem = sizeof(float) * (size_t)kTcStages * kStage;
+};
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
   constexpr uint32_t lbo = 128, sbo = (kTcKC / 4) * 128;
@@ -256,12 +264,12 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
   d |= (uint64_t)1 << 46;   // descriptor version; base offset 0, no swizzle
   return d;
 }
-// kind::tf32 instruction descriptor: D F32, A and B TF32, both K-major
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) |
+// kind::tf32 instruction descriptor: D F32, A and B TF32, both K-major, M = N = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTileTC >> 3) << 17) |
                               ((uint32_t)(kTileTC >> 4) << 24);
 
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < kTcWaitIters; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -273,243 +281,303 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tc_cp4(uint32_t dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
+  return __uint_as_float(h);
 }
 
-// Producer state: the contribution being copied, with this thread's fixed
-// share of each chunk (8 elements of op(A), 4 of op(B)) as base pointers and
-// per-element strides, so a chunk costs one address add per element.
-struct TcProd {
-  int c, k0, K;
-  const float* pa;   // element (row ia, column ka) of op(A) at k0 = 0
-  const float* pb;
-  long long sa, sb;  // pointer step between this thread's elements q and q + 1
-  long long ka_step, kb_step;   // pointer step per unit of k0
-  int ia, ka, ja, kbb;          // this thread's first (row, k) of A and (row, k) of B
-  int dia, dka, djb, dkb;       // (row, k) step per element
+// The producers' position in the task's chunk sequence: contribution c, K
+// offset k0 (both advance chunk by chunk).
+struct TcCursor {
+  int c, k0;
 };
 
-__device__ __forceinline__ void tc_prod_set(TcProd& p, const GemmContrib<float>& cb) {
-  const int tid = threadIdx.x;
-  p.K = cb.K;
-  if (!(cb.flags & kTransA)) {   // op(A) = A, M x K column-major: rows contiguous
-    p.ia = tid & (kTileTC - 1); p.ka = tid >> 7; p.dia = 0; p.dka = 2;
-    p.pa = cb.A + p.ia + (size_t)p.ka * cb.lda;
-    p.sa = 2LL * cb.lda;
-    p.ka_step = cb.lda;
-  } else {                       // op(A) = A^T, A is K x M: k contiguous
-    p.ka = tid & (kTcKC - 1); p.ia = tid >> 4; p.dia = 16; p.dka = 0;
-    p.pa = cb.A + p.ka + (size_t)p.ia * cb.lda;
-    p.sa = 16LL * cb.lda;
-    p.ka_step = 1;
-  }
-  if (!(cb.flags & kTransB)) {   // op(B) = B, K x N column-major: k contiguous
-    p.kbb = tid & (kTcKC - 1); p.ja = tid >> 4; p.djb = 16; p.dkb = 0;
-    p.pb = cb.B + p.kbb + (size_t)p.ja * cb.ldb;
-    p.sb = 16LL * cb.ldb;
-    p.kb_step = 1;
-  } else {                       // op(B) = B^T, B is N x K: rows j contiguous
-    p.ja = tid & (kTile - 1); p.kbb = tid >> 6; p.djb = 0; p.dkb = 4;
-    p.pb = cb.B + p.ja + (size_t)p.kbb * cb.ldb;
-    p.sb = 4LL * cb.ldb;
-    p.kb_step = cb.ldb;
+__device__ __forceinline__ void tc_cursor_next(TcCursor& u, const GemmContrib<float>* __restrict__ cons, int cend) {
+  u.k0 += kTcKC;
+  if (u.k0 >= cons[u.c].K) {
+    u.k0 = 0;
+    ++u.c;
+    while (u.c < cend && cons[u.c].K <= 0) ++u.c;
   }
 }
 
-// copies of the producer's current chunk into a raw stage
-__device__ __forceinline__ void tc_issue(const TcProd& p, int M, int N, uint32_t sraw) {
-  const int kc = min(kTcKC, p.K - p.k0);
-  const float* a = p.pa + p.ka_step * p.k0;
+// Producer thread p (0..127) loads 16 values of op(A) and 16 of op(B)^T for
+// one chunk (zero outside the task / contribution).  Non-transposed A (rows
+// contiguous): row p, k = 0..15.  Transposed A (k contiguous): k group p mod 4
+// (four consecutive k), rows p / 4 + 32 j.  op(B)^T likewise with B^T playing
+// the role of A.
+__device__ __forceinline__ void tc_load(const GemmContrib<float>& cb, int k0, int M, int N, int p, float (&ra)[16],
+                                        float (&rb)[16]) {
+  const int kc = min(kTcKC, cb.K - k0);
+  if (!(cb.flags & kTransA)) {
+    const bool ok = p < M;
+    const float* a = cb.A + p + (size_t)k0 * cb.lda;
 #pragma unroll
-  for (int q = 0; q < kTcAOp / kThreads; ++q) {
-    const int i = p.ia + q * p.dia, k = p.ka + q * p.dka;
-    if (i < M && k < kc) tc_cp4(sraw + 4u * (k * kTcAP + i), a + q * p.sa);
+    for (int k = 0; k < 16; ++k) ra[k] = (ok && k < kc) ? __ldg(a + (size_t)k * cb.lda) : 0.f;
+  } else {
+    const int kq = p & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = (p >> 2) + 32 * j;
+      const float* a = cb.A + k0 + 4 * kq + (size_t)i * cb.lda;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ra[4 * j + e] = (i < M && 4 * kq + e < kc) ? __ldg(a + e) : 0.f;
+    }
   }
-  const float* b = p.pb + p.kb_step * p.k0;
+  if (cb.flags & kTransB) {   // op(B)^T = B, N x K, rows j contiguous
+    const bool ok = p < N;
+    const float* b = cb.B + p + (size_t)k0 * cb.ldb;
 #pragma unroll
-  for (int q = 0; q < kTcBOp / kThreads; ++q) {
-    const int j = p.ja + q * p.djb, k = p.kbb + q * p.dkb;
-    if (j < N && k < kc) tc_cp4(sraw + 4u * (kTcARaw + k * kTcBP + j), b + q * p.sb);
+    for (int k = 0; k < 16; ++k) rb[k] = (ok && k < kc) ? __ldg(b + (size_t)k * cb.ldb) : 0.f;
+  } else {                    // op(B) = B, K x N column-major: k contiguous
+    const int kq = p & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = (p >> 2) + 32 * j;
+      const float* b = cb.B + k0 + 4 * kq + (size_t)i * cb.ldb;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) rb[4 * j + e] = (i < N && 4 * kq + e < kc) ? __ldg(b + e) : 0.f;
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_gemm_tc(const GemmTask<float>* __restrict__ tasks,
-                                                      const GemmContrib<float>* __restrict__ cons) {
+// split 16 values of one operand into NPART parts and store them; rowk: the
+// values are row p, k = 0..15; else rows p / 4 + 32 q, k = 4 (p mod 4) + e
+template <int NPART>
+__device__ __forceinline__ void tc_store(float* base, bool rowk, int p, const float (&r)[16]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int row, kq;
+    if (rowk) { row = p; kq = q; } else { row = (p >> 2) + 32 * q; kq = p & 3; }
+    const int off = (row >> 3) * (kTcKC / 4) * 32 + kq * 32 + (row & 7) * 4;   // floats
+    float v[4] = {r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]};
+#pragma unroll
+    for (int part = 0; part < NPART; ++part) {
+      float4 o;
+      float* po = reinterpret_cast<float*>(&o);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float h = tf32_rna(v[e]);
+        po[e] = h;
+        v[e] -= h;
+      }
+      *reinterpret_cast<float4*>(base + part * kTcPartA + off) = o;
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+template <int NPART>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>* __restrict__ tasks,
+                                                           const GemmContrib<float>* __restrict__ cons) {
+  using Cfg = TcCfg<NPART>;
   const GemmTask<float> tk = tasks[blockIdx.x];
   extern __shared__ __align__(1024) unsigned char tc_smraw[];
-  float* ops = reinterpret_cast<float*>(tc_smraw);        // 2 x [Ah | Al | Bh | Bl]
-  float* raw = ops + 2 * kTcOp;                           // kTcStages x [rawA | rawB]
-  __shared__ __align__(8) uint64_t mbar[2];
+  float* stg = reinterpret_cast<float*>(tc_smraw);   // kTcStages x [A parts | B parts]
+  // full[s], empty[s], acc_full[2], acc_empty[2], done
+  __shared__ __align__(8) uint64_t mbar[2 * kTcStages + 5];
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
-  const uint32_t sraw0 = (uint32_t)__cvta_generic_to_shared(raw);
-  if (warp == 0) {
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+  auto full = [&](int st) { return mb + 8u * st; };
+  auto empty = [&](int st) { return mb + 8u * (kTcStages + st); };
+  auto acc_full = [&](int b) { return mb + 8u * (2 * kTcStages + b); };
+  auto acc_empty = [&](int b) { return mb + 8u * (2 * kTcStages + 2 + b); };
+  const uint32_t done = mb + 8u * (2 * kTcStages + 4);
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
-                 "r"(kTile)
+                 "r"(2 * kTileTC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0 + 8) : "memory");
+    for (int st = 0; st < kTcStages; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full(st)), "r"(128) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(st)) : "memory");
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(acc_full(b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(acc_empty(b)), "r"(128) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(done) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_bad = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const int M = tk.M, N = tk.N, cend = tk.c_begin + tk.c_count;
-  // producer (copies) and consumer (split + products) cursors
-  TcProd pr;
-  pr.c = tk.c_begin;
-  while (pr.c < cend && cons[pr.c].K <= 0) ++pr.c;
-  pr.k0 = 0;
-  if (pr.c < cend) tc_prod_set(pr, cons[pr.c]);
-  int cc = pr.c, ck0 = 0, cK = pr.c < cend ? pr.K : 0;
-  auto prod_advance = [&]() {
-    pr.k0 += kTcKC;
-    if (pr.k0 >= pr.K) {
-      pr.k0 = 0;
-      ++pr.c;
-      while (pr.c < cend && cons[pr.c].K <= 0) ++pr.c;
-      if (pr.c < cend) tc_prod_set(pr, cons[pr.c]);
-    }
-  };
+  int nch = 0;
+  for (int c = tk.c_begin; c < cend; ++c) nch += (max(cons[c].K, 0) + kTcKC - 1) / kTcKC;
+  const int ngrp = (nch + kTcFlush - 1) / kTcFlush;
+
+  if (warp < 4) {
+    // ---- producers
+    const int p = tid;
+    TcCursor ld{tk.c_begin, 0};
+    while (ld.c < cend && cons[ld.c].K <= 0) ++ld.c;
+    TcCursor sp = ld;   // the chunk being stored (its contribution's layout flags)
+    float ra[3][16], rb[3][16];
+    auto load_next = [&](float (&a)[16], float (&b)[16]) {
+      const GemmContrib<float> cb = cons[ld.c];
+      tc_load(cb, ld.k0, M, N, p, a, b);
+      tc_cursor_next(ld, cons, cend);
+    };
+    if (nch > 0) load_next(ra[0], rb[0]);
+    if (nch > 1) load_next(ra[1], rb[1]);
+    bool bad = false;
+    for (int c0 = 0; c0 < nch && !bad; c0 += 3) {
 #pragma unroll
-  for (int st = 0; st < kTcStages - 1; ++st) {
-    if (pr.c < cend) {
-      tc_issue(pr, M, N, sraw0 + 4u * st * kTcStage);
-      prod_advance();
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
-  // split work: core matrices (8 rows x 4 k) holding real rows, one per warp step
-  const int acm = ((M + 7) >> 3) * (kTcKC / 4), bcm = ((N + 7) >> 3) * (kTcKC / 4);
-  const int lr = lane >> 2, lk = lane & 3;
-  int i = 0;
-  uint32_t ph[2] = {0u, 0u};
-  bool bad = false;
-  while (cc < cend) {
-    if (pr.c < cend) {   // its stage held chunk i - 1, split last iteration
-      tc_issue(pr, M, N, sraw0 + 4u * ((i + kTcStages - 1) % kTcStages) * kTcStage);
-      prod_advance();
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcStages - 1) : "memory");
-    __syncthreads();   // chunk i landed for every thread
-    const int bsel = i & 1;
-    if (i >= 2) {      // products of chunk i - 2 must be done with this operand buffer
-      if (!tc_wait(mb0 + 8 * bsel, ph[bsel])) { bad = true; break; }
-      ph[bsel] ^= 1;
-    }
-    {
-      const int kc = min(kTcKC, cK - ck0);
-      const float* rA = raw + (i % kTcStages) * kTcStage;
-      const float* rB = rA + kTcARaw;
-      float* Ah = ops + bsel * kTcOp;
-      float* Al = Ah + kTcAOp;
-      float* Bh = Al + kTcAOp;
-      float* Bl = Bh + kTcBOp;
-      for (int cm = warp; cm < acm; cm += kThreads / 32) {
-        const int g = cm / (kTcKC / 4), kq = cm - g * (kTcKC / 4);
-        const int k = 4 * kq + lk, row = 8 * g + lr;
-        const float v = k < kc ? rA[k * kTcAP + row] : 0.f;
-        uint32_t h;
-        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
-        Ah[32 * cm + lane] = __uint_as_float(h);   // core matrix (g, kq): 32 contiguous floats
-        Al[32 * cm + lane] = v - __uint_as_float(h);
-      }
-      for (int cm = warp; cm < bcm; cm += kThreads / 32) {
-        const int g = cm / (kTcKC / 4), kq = cm - g * (kTcKC / 4);
-        const int k = 4 * kq + lk, row = 8 * g + lr;
-        const float v = k < kc ? rB[k * kTcBP + row] : 0.f;
-        uint32_t h;
-        asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
-        Bh[32 * cm + lane] = __uint_as_float(h);
-        Bl[32 * cm + lane] = v - __uint_as_float(h);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t sAh = (uint32_t)__cvta_generic_to_shared(ops + bsel * kTcOp);
-      const uint32_t sAl = sAh + 4 * kTcAOp, sBh = sAl + 4 * kTcAOp, sBl = sBh + 4 * kTcBOp;
-#pragma unroll
-      for (int st = 0; st < kTcKC / 8; ++st) {
-        const uint32_t ko = st * 2 * 128;   // two core matrices along K per step
-        const uint64_t ah = tc_desc(sAh + ko), al = tc_desc(sAl + ko);
-        const uint64_t bh = tc_desc(sBh + ko), bl = tc_desc(sBl + ko);
-        const uint64_t ad[3] = {ah, ah, al}, bd[3] = {bh, bl, bh};
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const uint32_t accum = (i > 0 || st > 0 || t > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad[t]), "l"(bd[t]), "r"(kTcIdesc), "r"(accum)
-              : "memory");
+      for (int u = 0; u < 3; ++u) {
+        const int c = c0 + u;
+        if (c < nch && !bad) {
+          if (c + 2 < nch) load_next(ra[(u + 2) % 3], rb[(u + 2) % 3]);
+          const int st = c % kTcStages;
+          if (c >= kTcStages && !tc_wait(empty(st), (uint32_t)(((c / kTcStages) + 1) & 1))) {
+            bad = true;
+            break;
+          }
+          const int fl = cons[sp.c].flags;
+          float* base = stg + st * Cfg::kStage;
+          tc_store<NPART>(base, !(fl & kTransA), p, ra[u]);
+          tc_store<NPART>(base + NPART * kTcPartA, (fl & kTransB) != 0, p, rb[u]);
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full(st)) : "memory");
+          tc_cursor_next(sp, cons, cend);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                       mb0 + 8 * bsel)
+    }
+    if (bad) atomicExch(&s_bad, 1);
+  } else if (warp == 4) {
+    // ---- MMA issue (one thread)
+    if (lane == 0) {
+      bool bad = false;
+      for (int g = 0; g < ngrp && !bad; ++g) {
+        const int b = g & 1;
+        if (g >= 2 && !tc_wait(acc_empty(b), (uint32_t)(((g >> 1) + 1) & 1))) {
+          bad = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(b * kTileTC);
+        const int c1 = min(nch, (g + 1) * kTcFlush);
+        for (int c = g * kTcFlush; c < c1; ++c) {
+          const int st = c % kTcStages;
+          if (!tc_wait(full(st), (uint32_t)((c / kTcStages) & 1))) {
+            bad = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t sA = (uint32_t)__cvta_generic_to_shared(stg + st * Cfg::kStage);
+          const uint32_t sB = sA + 4u * NPART * kTcPartA;
+#pragma unroll
+          for (int ks = 0; ks < kTcKC / 8; ++ks) {
+            const uint32_t ko = ks * 2 * 128;   // two core matrices along K per step
+            // products p_i q_j with i + j < NPART, the small ones first
+#pragma unroll
+            for (int deg = NPART - 1; deg >= 0; --deg)
+#pragma unroll
+              for (int i = 0; i <= deg; ++i) {
+                const int j = deg - i;
+                const uint64_t ad = tc_desc(sA + 4u * i * kTcPartA + ko);
+                const uint64_t bd = tc_desc(sB + 4u * j * kTcPartA + ko);
+                const uint32_t accum = (c > g * kTcFlush || ks > 0 || deg < NPART - 1 || i > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
+                    "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(accum)
+                    : "memory");
+              }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           empty(st))
+                       : "memory");
+        }
+        // the group's partial sum is complete once its products are
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         acc_full(b))
+                     : "memory");
+      }
+      // tracks every product issued above, whether or not the loops finished
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
                    : "memory");
+      if (bad) atomicExch(&s_bad, 1);
     }
-    // consumer cursor
-    ck0 += kTcKC;
-    if (ck0 >= cK) {
-      ck0 = 0;
-      ++cc;
-      while (cc < cend && cons[cc].K <= 0) ++cc;
-      cK = cc < cend ? cons[cc].K : 0;
+    __syncwarp();
+  } else {
+    // ---- accumulators: warp w reads tensor-memory lanes 32 (w mod 4) .. + 31
+    const int qd = warp & 3;
+    const int row = 32 * qd + lane;
+    float acc[kTileTC];
+#pragma unroll
+    for (int j = 0; j < kTileTC; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int g = 0; g < ngrp; ++g) {
+      const int b = g & 1;
+      if (ok && !tc_wait(acc_full(b), (uint32_t)((g >> 1) & 1))) ok = false;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int h = 0; h < kTileTC / 64; ++h) {
+        uint32_t r0[32], r1[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * kTileTC + 64 * h);
+        tmem_ld32(taddr, r0);
+        tmem_ld32(taddr + 32, r1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          acc[64 * h + t] += __uint_as_float(r0[t]);
+          acc[64 * h + 32 + t] += __uint_as_float(r1[t]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acc_empty(b)) : "memory");
     }
-    ++i;
-  }
-  // products still outstanding: the last two chunks' buffers
-  const int n = i;
-  for (int k = (n >= 2 ? n - 2 : 0); k < n; ++k) {
-    const int bsel = k & 1;
-    if (!tc_wait(mb0 + 8 * bsel, ph[bsel])) bad = true;
-    ph[bsel] ^= 1;
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  const int qd = warp & 3, half = warp >> 2;
-  const int row = 32 * qd + lane;
-  uint32_t r[32];
+    if (!ok) atomicExch(&s_bad, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();   // (1) every role has finished its loop and recorded failures
+    const bool poisoned = s_bad != 0;
+    if (row < M) {
 #pragma unroll
-  for (int t = 0; t < 32; ++t) r[t] = 0u;
-  if (n > 0 && !bad) {
-    const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(32 * half);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-  }
-  if (row < M) {
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int j = 32 * half + t;
-      if (j < N) {
-        float* p = tk.C + (size_t)row + (size_t)j * tk.ldc;
-        float v = bad ? __int_as_float(0x7fc00000) : tk.alpha * __uint_as_float(r[t]);
-        if (tk.beta) v += *p;
-        *p = v;
+      for (int j = 0; j < kTileTC; ++j) {
+        if (j < N) {
+          float* pc = tk.C + (size_t)row + (size_t)j * tk.ldc;
+          if (nch == 0) {
+            if (!tk.beta) *pc = 0.f;
+          } else {
+            float v = poisoned ? __int_as_float(0x7fc00000) : tk.alpha * acc[j];
+            if (tk.beta) v += *pc;
+            *pc = v;
+          }
+        }
       }
     }
+    return;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTile) : "memory");
+  __syncthreads();   // (1)
+  if (warp == 4) {
+    // the tensor memory is released only once every product issued has
+    // completed (the commit tracks them all), or the bounded wait gave up
+    tc_wait(done, 0u);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kTileTC)
+                 : "memory");
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -527,7 +595,7 @@ constexpr int kPitch = kTile + 1;
 // is a forward substitution per column of V, each owned by four lanes of one
 // warp, so its row steps need only warp synchronisation.
 template <typename T>
-__device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
+__device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V, const T* d0) {
   __shared__ int bad;
   __shared__ T dinv[kTile];   // d_j^{-1/2}
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
@@ -540,9 +608,10 @@ __device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
   int mybad = 0;
   for (int j = 0; j < n; ++j) {
     T d = S[j * kPitch + j];
-    if (!(d > T(0)) || !isfinite(d)) {
+    const bool lost = sizeof(T) == 4 && d0 && d <= T(kPivotLoss) * d0[j];
+    if (!(d > T(0)) || !isfinite(d) || lost) {
       mybad = isfinite(d) ? 1 : 2;
-      d = T(1);
+      if (!(d > T(0)) || !isfinite(d)) d = T(1);
     }
     const T rd = T(1) / d;
     // trailing lower triangle, 16 x 16 thread grid; column j itself is read only
@@ -592,7 +661,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagTask<T>* __restrict
   extern __shared__ __align__(16) unsigned char smraw[];
   T* S = reinterpret_cast<T*>(smraw);
   T* V = S + kTile * kPitch;
-  const int bad = diag_tile<T>(tk.A, tk.lda, tk.Li, tk.ldli, tk.n, S, V);
+  const int bad = diag_tile<T>(tk.A, tk.lda, tk.Li, tk.ldli, tk.n, S, V, tk.d0);
   if (threadIdx.x == 0 && bad) report(st, bad == 1 ? SGF_ERR_NOT_SPD : SGF_ERR_NONFINITE, level, tk.node);
 }
 
@@ -770,7 +839,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const FrontTask<T>* __res
   for (int k = 0; k < nt; ++k) {
     const int r0 = k * kTile, nk = min(kTile, m - r0), r1 = r0 + nk;
     T* Likk = Li + r0 + (size_t)r0 * m;
-    const int b = diag_tile<T>(D + r0 + (size_t)r0 * m, m, Likk, m, nk, S, V);
+    const int b = diag_tile<T>(D + r0 + (size_t)r0 * m, m, Likk, m, nk, S, V, tk.d0 ? tk.d0 + r0 : nullptr);
     if (b && !bad) bad = b;
     for (int ri = r1; ri < m; ri += kTile) {
       T* C = D + ri + (size_t)r0 * m;
@@ -1072,6 +1141,142 @@ __device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
+// Warp-granular GEMVs for chunks too small to fill a CTA (unsplit tasks of
+// at most kGemvWarpElems elements, see GemvList::emit): they ride in the same
+// launch as the CTA tasks, eight to a block, one per warp, with no shared
+// staging and no barrier.  Each output's sum runs over its contributions in
+// order, lane l taking the rows (op T) or columns (op N) l, l + 32, ... of
+// each, then a butterfly (op T) - the same order for every NR.
+//
+// op(A) = A^T: the warp walks the chunk's outputs CW at a time (their loads
+// interleaved); each column is read only over its useful rows (a triangular
+// block's zero half is skipped per column).
+template <typename T, int NR>
+__device__ __forceinline__ void gemv_tw_one(const GemvTask<T>& tk, const GemvContrib<T>* __restrict__ cons, int lane) {
+  constexpr int CW = NR <= 2 ? 4 : 2;
+  constexpr int U = sizeof(T) == 4 ? 4 : 2;   // row steps in flight
+  for (int o0 = 0; o0 < tk.M; o0 += CW) {
+    T acc[CW][NR];
+#pragma unroll
+    for (int u = 0; u < CW; ++u)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[u][q] = T(0);
+    for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
+      const GemvContrib<T> cb = cons[c];
+      const T* col[CW];
+      int lo[CW], hi[CW];
+      int rlo = cb.K, rhi = 0;
+#pragma unroll
+      for (int u = 0; u < CW; ++u) {
+        const int o = o0 + u;
+        col[u] = cb.A + (size_t)o * cb.lda;
+        lo[u] = 0;
+        hi[u] = o < tk.M ? cb.K : 0;
+        if (cb.tri && o < tk.M) {
+          if (cb.upper) hi[u] = min(cb.K, cb.tri + o);   // rows <= absolute column tri - 1 + o
+          else lo[u] = cb.tri - 1 + o;                    // rows >= it
+        }
+        if (hi[u] > lo[u]) {
+          rlo = min(rlo, lo[u]);
+          rhi = max(rhi, hi[u]);
+        }
+      }
+#pragma unroll U
+      for (int i = rlo + lane; i < rhi; i += 32) {
+        T xv[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          T v = cb.x[(size_t)i * NR + q];
+          if (cb.x2) v -= cb.x2[(size_t)i * NR + q];
+          xv[q] = cb.alpha * v;
+        }
+        T av[CW];
+#pragma unroll
+        for (int u = 0; u < CW; ++u) av[u] = (i >= lo[u] && i < hi[u]) ? col[u][i] : T(0);
+#pragma unroll
+        for (int u = 0; u < CW; ++u)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[u][q] = fma(av[u], xv[q], acc[u][q]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CW; ++u) {
+      const int o = o0 + u;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const T v = warp_sum(acc[u][q]);
+        if (lane == 0 && o < tk.M) {
+          T* y = tk.y + (size_t)o * NR + q;
+          *y = tk.beta ? *y + v : v;
+        }
+      }
+    }
+  }
+}
+
+// op(A) = A, chunks of at most kGemvWarpRows rows: lane l owns rows l, l + 32,
+// ... of the band (RP of them), so no reduction is needed; the warp walks
+// the columns of every contribution in order, U at a time.
+constexpr int kGemvWarpRows = kGemvWarpRowsMax;
+template <typename T, int NR>
+__device__ __forceinline__ void gemv_nw_one(const GemvTask<T>& tk, const GemvContrib<T>* __restrict__ cons, int lane) {
+  constexpr int RP = kGemvWarpRows / 32;
+  constexpr int U = 4;   // columns in flight
+  T acc[RP][NR];
+#pragma unroll
+  for (int r = 0; r < RP; ++r)
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[r][q] = T(0);
+  for (int c = tk.c_begin; c < tk.c_begin + tk.c_count; ++c) {
+    const GemvContrib<T> cb = cons[c];
+    int kb, ke;
+    gemv_useful(false, cb.tri, cb.upper, cb.K, tk.M, &kb, &ke);
+#pragma unroll U
+    for (int j = kb; j < ke; ++j) {
+      const T* colp = cb.A + (size_t)j * cb.lda;
+      const int rmin = cb.tri ? j - (cb.tri - 1) : 0;   // a lower-triangular block's zero rows
+      T xv[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        T v = cb.x[(size_t)j * NR + q];
+        if (cb.x2) v -= cb.x2[(size_t)j * NR + q];
+        xv[q] = cb.alpha * v;
+      }
+#pragma unroll
+      for (int r = 0; r < RP; ++r) {
+        const int row = lane + 32 * r;
+        const T a = (row < tk.M && row >= rmin) ? colp[row] : T(0);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[r][q] = fma(a, xv[q], acc[r][q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RP; ++r) {
+    const int row = lane + 32 * r;
+    if (row < tk.M) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        T* y = tk.y + (size_t)row * NR + q;
+        *y = tk.beta ? *y + acc[r][q] : acc[r][q];
+      }
+    }
+  }
+}
+
+// blocks beyond the CTA tasks carry the warp tasks, one per warp
+template <typename T, int NR, bool TRANS>
+__device__ __forceinline__ void gemv_warp_block(const GemvTask<T>* __restrict__ wtasks, int nw,
+                                                const GemvContrib<T>* __restrict__ cons, int block) {
+  pdl_trigger();
+  pdl_wait();   // x and y are written by earlier kernels
+  const int t = block * (kThreads / 32) + (threadIdx.x >> 5);
+  if (t >= nw) return;
+  const GemvTask<T> tk = wtasks[t];
+  if (TRANS) gemv_tw_one<T, NR>(tk, cons, threadIdx.x & 31);
+  else gemv_nw_one<T, NR>(tk, cons, threadIdx.x & 31);
+}
+
 // One column of an op N step: its x entries (scaled) and the band rows of the
 // current pass (zero outside the band and, for a lower-triangular block,
 // above the diagonal).
@@ -1107,11 +1312,13 @@ __device__ __forceinline__ void gemv_n_col(const GemvStage<T>& S, int& c, int f,
 // over the same columns in the same order for every NR.
 template <typename T, int NR, int MT>
 __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restrict__ tasks,
-                                                     const GemvContrib<T>* __restrict__ cons) {
+                                                     const GemvContrib<T>* __restrict__ cons, int ncta,
+                                                     const GemvTask<T>* __restrict__ wtasks, int nw) {
   constexpr int kWarps = kThreads / 32;
   constexpr int MP = MT / NR > 0 ? MT / NR : 1;   // 32-row groups per pass
   // two columns per step unless that would cost too many registers (FP64, wide bands)
   constexpr bool kTwo = sizeof(T) == 4 || MP <= 8;
+  if ((int)blockIdx.x >= ncta) return gemv_warp_block<T, NR, false>(wtasks, nw, cons, blockIdx.x - ncta);
   pdl_trigger();
   const GemvTask<T> tk = tasks[blockIdx.x];
   __shared__ GemvStage<T> S;
@@ -1186,9 +1393,10 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n(const GemvTask<T>* __restri
 // of each contribution, and the lane sums are combined by a butterfly.
 template <typename T, int NR, int CW>
 __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
-    k_gemv_t(const GemvTask<T>* __restrict__ tasks,
-                                                     const GemvContrib<T>* __restrict__ cons) {
+    k_gemv_t(const GemvTask<T>* __restrict__ tasks, const GemvContrib<T>* __restrict__ cons, int ncta,
+             const GemvTask<T>* __restrict__ wtasks, int nw) {
   constexpr int kWarps = kThreads / 32;
+  if ((int)blockIdx.x >= ncta) return gemv_warp_block<T, NR, true>(wtasks, nw, cons, blockIdx.x - ncta);
   pdl_trigger();
   const GemvTask<T> tk = tasks[blockIdx.x];
   __shared__ GemvStage<T> S;
@@ -1258,6 +1466,8 @@ __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
   }
   gemv_finish(tk, tk.M * NR);
 }
+
+
 
 // dst[p * nr + q] = src[idx[p] * nr + q]: gathers scattered level-vector
 // entries into one contiguous vector (nr interleaved right-hand sides)
@@ -1526,13 +1736,21 @@ __global__ void k_gather(const double* __restrict__ src, const int64_t* __restri
   for (int q = 0; q < nr; ++q) dst[i * nr + q] = q < nrhs ? (T)src[(int64_t)q * n + p] : T(0);
 }
 
+// also raises *nonfinite (when given) if a value written is NaN or infinite:
+// the flag costs no traffic unless it fires
 template <typename T>
 __global__ void k_scatter(const T* __restrict__ src, const int64_t* __restrict__ perm,
-                          double* __restrict__ dst, int64_t n, int nrhs, int nr) {
+                          double* __restrict__ dst, int64_t n, int nrhs, int nr, int* nonfinite) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t p = perm[i];
-  for (int q = 0; q < nrhs; ++q) dst[(int64_t)q * n + p] = (double)src[i * nr + q];
+  bool bad = false;
+  for (int q = 0; q < nrhs; ++q) {
+    const double v = (double)src[i * nr + q];
+    bad |= !isfinite(v);
+    dst[(int64_t)q * n + p] = v;
+  }
+  if (bad && nonfinite) atomicOr(nonfinite, 1);
 }
 
 __global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
@@ -1583,11 +1801,12 @@ bool gemm_tc_enabled() {
   return on;
 }
 
-void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* cons, int n, cudaStream_t s) {
+void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* cons, int n, int nparts, cudaStream_t s) {
   if (dry_run()) {
+    if (nparts != 2 && nparts != 3) check_range(nullptr, 1, "tc gemm split parts");
     for (int i = 0; i < n; ++i) {
       const GemmTask<float>& t = tasks[i];
-      if (t.M > kTileTC || t.N > kTile || t.M < 1 || t.N < 1) check_range(nullptr, 1, "tc gemm tile shape");
+      if (t.M > kTileTC || t.N > kTileTC || t.M < 1 || t.N < 1) check_range(nullptr, 1, "tc gemm tile shape");
       check_block(t.C, t.M, t.N, t.ldc, sizeof(float), "tc gemm C");
       for (int c = t.c_begin; c < t.c_begin + t.c_count; ++c) {
         const GemmContrib<float>& q = cons[c];
@@ -1602,11 +1821,13 @@ void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* cons
   if (n <= 0) return;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<2>::kSmem);
+    cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<3>::kSmem);
     attr = true;
   }
   ProfScope ps(P_GEMM, s);
-  k_gemm_tc<<<n, kThreads, kTcSmem, s>>>(tasks, cons);
+  if (nparts == 2) k_gemm_tc<2><<<n, kTcThreads, TcCfg<2>::kSmem, s>>>(tasks, cons);
+  else k_gemm_tc<3><<<n, kTcThreads, TcCfg<3>::kSmem, s>>>(tasks, cons);
 }
 
 template <typename T>
@@ -1616,6 +1837,7 @@ void launch_diag(const DiagTask<T>* tasks, int n, DevStatus* st, int level, cuda
       if (tasks[i].n > kTile || tasks[i].n < 1) check_range(nullptr, 1, "diag tile shape");
       check_block(tasks[i].A, tasks[i].n, tasks[i].n, tasks[i].lda, sizeof(T), "diag A");
       check_block(tasks[i].Li, tasks[i].n, tasks[i].n, tasks[i].ldli, sizeof(T), "diag Li");
+      if (tasks[i].d0) check_range(tasks[i].d0, sizeof(T) * tasks[i].n, "diag diagonal");
     }
     return;
   }
@@ -1636,6 +1858,7 @@ void launch_front(const FrontTask<T>* tasks, int n, DevStatus* st, int level, cu
     for (int i = 0; i < n; ++i) {
       check_block(tasks[i].D, tasks[i].m, tasks[i].m, tasks[i].m, sizeof(T), "front D");
       check_block(tasks[i].Li, tasks[i].m, tasks[i].m, tasks[i].m, sizeof(T), "front Li");
+      if (tasks[i].d0) check_range(tasks[i].d0, sizeof(T) * tasks[i].m, "front diagonal");
     }
     return;
   }
@@ -1724,20 +1947,29 @@ static void check_gemv(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int
   }
 }
 
+template <typename T>
+static void check_warp_tasks(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, bool trans, int nr) {
+  if (n <= 0) return;
+  for (int i = 0; i < n; ++i)
+    if (tasks[i].nsplit != 1 || (!trans && tasks[i].M > kGemvWarpRowsMax)) check_range(nullptr, 1, "warp gemv task shape");
+  check_gemv(tasks, cons, n, trans, nr, trans ? kGemvColsMax : kGemvWarpRowsMax);
+}
+
 namespace {
 thread_local bool t_dependent = false;
 
 // <<<grid, kThreads>>> launch, with the programmatic-serialization attribute
 // while dependent launch is on for this thread
 template <typename... KArgs, typename... Args>
-void launch_apply_kernel(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+void launch_apply_kernel_smem(void (*kern)(KArgs...), unsigned grid, size_t smem, cudaStream_t s, Args... args) {
   if (!t_dependent) {
-    kern<<<grid, kThreads, 0, s>>>(args...);
+    kern<<<grid, kThreads, smem, s>>>(args...);
     return;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1747,6 +1979,10 @@ void launch_apply_kernel(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, 
   // a failed launch is reported like a <<<>>> launch: by the caller's
   // cudaGetLastError, or by the end of the stream capture it belongs to
   (void)cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+template <typename... KArgs, typename... Args>
+void launch_apply_kernel(void (*kern)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+  launch_apply_kernel_smem(kern, grid, 0, s, args...);
 }
 }  // namespace
 
@@ -1760,49 +1996,61 @@ bool dependent_launch_enabled() {
 
 void set_dependent_launch(bool on) { t_dependent = on && dependent_launch_enabled(); }
 
+// grid: the CTA tasks, then one block per eight warp tasks
+inline unsigned gemv_grid(int n, int nw) { return (unsigned)(n + (nw + kThreads / 32 - 1) / (kThreads / 32)); }
+
 template <typename T, int NR>
-static void gemv_n_mt(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int max_m, cudaStream_t s) {
-  if (max_m <= 256) launch_apply_kernel(k_gemv_n<T, NR, 8>, n, s, tasks, cons);
-  else launch_apply_kernel(k_gemv_n<T, NR, 16>, n, s, tasks, cons);
+static void gemv_n_mt(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int max_m,
+                      const GemvTask<T>* wt, int nw, cudaStream_t s) {
+  if (max_m <= 256) launch_apply_kernel(k_gemv_n<T, NR, 8>, gemv_grid(n, nw), s, tasks, cons, n, wt, nw);
+  else launch_apply_kernel(k_gemv_n<T, NR, 16>, gemv_grid(n, nw), s, tasks, cons, n, wt, nw);
 }
 
 template <typename T>
 void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, int max_m,
-                   cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, false, nr, max_m);
-  if (n <= 0) return;
+                   cudaStream_t s, const GemvTask<T>* wtasks, int nw) {
+  if (dry_run()) {
+    check_warp_tasks(wtasks, cons, nw, false, nr);
+    return check_gemv(tasks, cons, n, false, nr, max_m);
+  }
+  if (n + nw <= 0) return;
   ProfScope ps(P_GEMV_N, s);
   switch (nr) {
-    case 1: gemv_n_mt<T, 1>(tasks, cons, n, max_m, s); break;
-    case 2: gemv_n_mt<T, 2>(tasks, cons, n, max_m, s); break;
-    case 4: gemv_n_mt<T, 4>(tasks, cons, n, max_m, s); break;
-    default: gemv_n_mt<T, 8>(tasks, cons, n, max_m, s); break;
+    case 1: gemv_n_mt<T, 1>(tasks, cons, n, max_m, wtasks, nw, s); break;
+    case 2: gemv_n_mt<T, 2>(tasks, cons, n, max_m, wtasks, nw, s); break;
+    case 4: gemv_n_mt<T, 4>(tasks, cons, n, max_m, wtasks, nw, s); break;
+    default: gemv_n_mt<T, 8>(tasks, cons, n, max_m, wtasks, nw, s); break;
   }
 }
 
 // the 64-wide chunks exist in single precision only (double-precision
 // accumulators of 8 columns x 8 right-hand sides would not fit the registers)
 template <typename T, int NR>
-static void gemv_t_cw(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int cols, cudaStream_t s) {
+static void gemv_t_cw(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int cols,
+                      const GemvTask<T>* wt, int nw, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     if (cols > kGemvCols) {
-      launch_apply_kernel(k_gemv_t<T, NR, kGemvColsMax / (kThreads / 32)>, n, s, tasks, cons);
+      launch_apply_kernel(k_gemv_t<T, NR, kGemvColsMax / (kThreads / 32)>, gemv_grid(n, nw), s, tasks, cons, n, wt, nw);
       return;
     }
   }
-  launch_apply_kernel(k_gemv_t<T, NR, kGemvCols / (kThreads / 32)>, n, s, tasks, cons);
+  launch_apply_kernel(k_gemv_t<T, NR, kGemvCols / (kThreads / 32)>, gemv_grid(n, nw), s, tasks, cons, n, wt, nw);
 }
 
 template <typename T>
-void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, int cols, cudaStream_t s) {
-  if (dry_run()) return check_gemv(tasks, cons, n, true, nr, cols);
-  if (n <= 0) return;
+void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* cons, int n, int nr, int cols, cudaStream_t s,
+                   const GemvTask<T>* wtasks, int nw) {
+  if (dry_run()) {
+    check_warp_tasks(wtasks, cons, nw, true, nr);
+    return check_gemv(tasks, cons, n, true, nr, cols);
+  }
+  if (n + nw <= 0) return;
   ProfScope ps(P_GEMV_T, s);
   switch (nr) {
-    case 1: gemv_t_cw<T, 1>(tasks, cons, n, cols, s); break;
-    case 2: gemv_t_cw<T, 2>(tasks, cons, n, cols, s); break;
-    case 4: gemv_t_cw<T, 4>(tasks, cons, n, cols, s); break;
-    default: gemv_t_cw<T, 8>(tasks, cons, n, cols, s); break;
+    case 1: gemv_t_cw<T, 1>(tasks, cons, n, cols, wtasks, nw, s); break;
+    case 2: gemv_t_cw<T, 2>(tasks, cons, n, cols, wtasks, nw, s); break;
+    case 4: gemv_t_cw<T, 4>(tasks, cons, n, cols, wtasks, nw, s); break;
+    default: gemv_t_cw<T, 8>(tasks, cons, n, cols, wtasks, nw, s); break;
   }
 }
 
@@ -1902,7 +2150,7 @@ void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, in
 }
 template <typename T>
 void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, int nrhs, int nr,
-                    cudaStream_t s) {
+                    cudaStream_t s, int* nonfinite) {
   if (dry_run()) {
     check_range(perm, 8 * n, "scatter perm");
     check_range(src, sizeof(T) * n * nr, "scatter src");
@@ -1911,7 +2159,7 @@ void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, i
   if (n <= 0) return;
   prof_work(0, (8.0 + (8.0 + sizeof(T)) * nrhs) * n);
   ProfScope ps(P_VEC, s);
-  k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n, nrhs, nr);
+  k_scatter<T><<<blocks_for(n), kThreads, 0, s>>>(src, perm, dst, n, nrhs, nr, nonfinite);
 }
 
 void launch_dot_n(const double* a, const double* b, int64_t n, int nrhs, double* partials, double* result,
@@ -1968,9 +2216,9 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
   template void launch_qrcp<T>(const QrTask<T>*, int, int*, double, int, int, long long,        \
                                cudaStream_t);                                                    \
   template void launch_gemv_n<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int, int,      \
-                                 cudaStream_t);                                                  \
+                                 cudaStream_t, const GemvTask<T>*, int);                         \
   template void launch_gemv_t<T>(const GemvTask<T>*, const GemvContrib<T>*, int, int, int,      \
-                                 cudaStream_t);                                                  \
+                                 cudaStream_t, const GemvTask<T>*, int);                         \
   template void launch_veccopy<T>(const VecCopyTask*, int, const T*, T*, cudaStream_t);         \
   template void launch_vgather<T>(const T*, const int*, T*, int, int, cudaStream_t);           \
   template void launch_assemble_scalar<T>(const double*, int, int, int, unsigned, double,       \
@@ -1982,7 +2230,7 @@ void launch_xpay(const double* z, double b, double* p, int64_t n, cudaStream_t s
   template void launch_gather<T>(const double*, const int64_t*, T*, int64_t, int, int,          \
                                  cudaStream_t);                                                  \
   template void launch_scatter<T>(const T*, const int64_t*, double*, int64_t, int, int,         \
-                                  cudaStream_t);
+                                  cudaStream_t, int*);
 
 SGF_INST(double)
 SGF_INST(float)

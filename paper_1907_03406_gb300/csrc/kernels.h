@@ -12,16 +12,18 @@ struct DevStatus {
   int code;   // 0 or an SGF_ERR_* value
   int level;
   int node;
-  int pad;
+  int nonfinite;   // an apply or multiply wrote a NaN / infinity (sgf_sync reads and clears it)
 };
 
 template <typename T>
 void launch_gemm(const GemmTask<T>* tasks, const GemmContrib<T>* contribs, int ntasks,
                  cudaStream_t s);
-// FP32 GEMM tasks of up to kTileTC x kTile on the 5th-generation tensor
-// cores: products split into TF32 high and low parts (a_hi b_hi + a_hi b_lo +
-// a_lo b_hi, "3xTF32"), FP32 accumulators in tensor memory
-void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* contribs, int ntasks,
+// FP32 GEMM tasks of up to kTileTC x kTileTC on the 5th-generation tensor
+// cores, FP32 accumulators in tensor memory.  Every operand is split into
+// nparts TF32 parts and the products p_i q_j with i + j < nparts are summed:
+// nparts = 2 is the 3xTF32 scheme (products accurate to ~2^-21), nparts = 3
+// carries them to FP32 accuracy with six products.
+void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* contribs, int ntasks, int nparts,
                     cudaStream_t s);
 // tensor-core GEMMs for the FP32 factor unless SGF_TENSOR_CORES=0
 bool gemm_tc_enabled();
@@ -58,16 +60,21 @@ void launch_qrcp(const QrTask<T>* tasks, int ntasks, int* ranks, double tau, int
                  long long cap_elems, cudaStream_t s);
 size_t qr_smem_bytes(int m, int c, size_t elem_size, long long cap_elems);
 // nr right-hand sides interleaved (nr in 1, 2, 4, 8)
-// max_m: largest chunk of the launch (op N bands up to 256 rows use a
-// narrower kernel)
+// max_m: largest chunk of the launch's CTA tasks (op N bands up to 256 rows
+// use a narrower kernel).  wtasks / nw: chunks too small to fill a CTA
+// (unsplit, at most kGemvWarpElems elements; op N bands of at most
+// kGemvWarpRowsMax rows), run in the same launch one per warp, eight to a
+// block after the CTA tasks' blocks (best ordered largest first).
+constexpr int kGemvWarpRowsMax = 128;
+constexpr int kGemvWarpElems = 4 * 1024;
 template <typename T>
 void launch_gemv_n(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr, int max_m,
-                   cudaStream_t s);
+                   cudaStream_t s, const GemvTask<T>* wtasks = nullptr, int nw = 0);
 // cols: the chunk width the tasks were built with (kGemvCols, or
 // kGemvColsMax in single precision)
 template <typename T>
 void launch_gemv_t(const GemvTask<T>* tasks, const GemvContrib<T>* contribs, int ntasks, int nr, int cols,
-                   cudaStream_t s);
+                   cudaStream_t s, const GemvTask<T>* wtasks = nullptr, int nw = 0);
 // dst[p * nr + q] = src[idx[p] * nr + q], p < n
 template <typename T>
 void launch_vgather(const T* src, const int* idx, T* dst, int n, int nr, cudaStream_t s);
@@ -103,9 +110,10 @@ void launch_dot(const double* a, const double* b, int64_t n, double* partials, d
 template <typename T>
 void launch_gather(const double* src, const int64_t* perm, T* dst, int64_t n, int nrhs, int nr,
                    cudaStream_t s);
+// nonfinite (may be null): raised to 1 when a value written is NaN or infinite
 template <typename T>
 void launch_scatter(const T* src, const int64_t* perm, double* dst, int64_t n, int nrhs, int nr,
-                    cudaStream_t s);
+                    cudaStream_t s, int* nonfinite = nullptr);
 
 // block PCG helpers on RHS-major FP64 vectors (nrhs <= 8)
 struct Coef8 {

@@ -57,6 +57,9 @@ extern "C" int sgf_pcg_solve_noalloc(const sgf_factor_t* fh, const double* b, do
   sgf::FactorBase& F = *fh->f;
   const int64_t n = F.n;
   if (n > (int64_t)SGF_NOALLOC_MAX_UNKNOWNS) return SGF_ERR_INVALID_ARG;  // beyond the fixed scratch
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return SGF_ERR_CUDA;
+  if (cur != F.device) return SGF_ERR_INVALID_ARG;   // the scratch array of another GPU
   double* ws = nullptr;
   int rc = scratch_for_current_device(&ws);
   if (rc != SGF_OK) return rc;

@@ -1,6 +1,8 @@
 // Launch accounting (see prof.h).
 #include "prof.h"
 
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -14,12 +16,14 @@ struct Acc {
 struct Pending {
   cudaEvent_t a, b;
   int kind;
+  double flops, bytes;
 };
 struct State {
   std::mutex mu;
   Acc acc[P_NKINDS];
   int timing = 0;
   double next_flops = 0, next_bytes = 0;
+  double next_flops_seen = 0, next_bytes_seen = 0;   // work of the launch being opened
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
 };
@@ -38,11 +42,17 @@ cudaEvent_t get_event(State& S) {
   cudaEventCreate(&e);
   return e;
 }
+// SGF_PROF_LOG=1: every timed launch is also printed to stderr (kind, its
+// algorithmic flops and bytes, device time), in launch order
+const bool g_log = std::getenv("SGF_PROF_LOG") != nullptr;
 void drain(State& S) {
   for (auto& p : S.pending) {
     cudaEventSynchronize(p.b);
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) S.acc[p.kind].ms += ms;
+    if (g_log)
+      std::fprintf(stderr, "[sgf launch] %-10s flops %.4e bytes %.4e ms %.5f GB/s %.1f\n", prof_name(p.kind),
+                   p.flops, p.bytes, ms, ms > 0 ? p.bytes / (ms * 1e-3) / 1e9 : 0.0);
     S.pool.push_back(p.a);
     S.pool.push_back(p.b);
   }
@@ -68,6 +78,8 @@ ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
   a.launches++;
   a.flops += S.next_flops;
   a.bytes += S.next_bytes;
+  S.next_flops_seen = S.next_flops;
+  S.next_bytes_seen = S.next_bytes;
   S.next_flops = S.next_bytes = 0;
   const bool timed = S.timing == 1 || (S.timing == 2 && (kind == P_GEMM || kind == P_DIAG || kind == P_QR || kind == P_APPLY));
   if (timed) {
@@ -75,6 +87,8 @@ ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
     p.a = get_event(S);
     p.b = get_event(S);
     p.kind = kind;
+    p.flops = S.next_flops_seen;
+    p.bytes = S.next_bytes_seen;
     cudaEventRecord(p.a, s);
     S.pending.push_back(p);
     slot_ = (int)S.pending.size() - 1;

@@ -74,7 +74,7 @@ struct Plan {
   std::vector<int64_t> asm_map, perm1;
   std::vector<int> asm_ld;         // Q1: level-1 node size of every point
   // launch shapes (sgf_tuning; see sgf_plan_set_tuning)
-  sgf_tuning tune{4096, 32768, 512, 1, 32};
+  sgf_tuning tune{4096, 32768, 512, 1, 32, 64};
 
   // device copies of the plan's constant data, built on first use
   struct DevCache {
@@ -121,12 +121,12 @@ int analyze(const sgf_grid* g, int stencil, const sgf_opts* o, Plan& plan, std::
 // Device task descriptors (one CTA per task unless stated)
 // ---------------------------------------------------------------------------
 constexpr int kTile = 64;
-constexpr int kTileTC = 128;   // rows of a tensor-core GEMM tile (columns: kTile)
+constexpr int kTileTC = 128;   // rows and columns of a tensor-core GEMM tile
 
 template <typename T>
 struct GemmTask {        // C[M x N] = beta*C + alpha * sum_c op(A_c) op(B_c)
   T* C;
-  int ldc, M, N;         // M <= kTile (kTileTC on the tensor-core path), N <= kTile
+  int ldc, M, N;         // M, N <= kTile (kTileTC on the tensor-core path)
   int c_begin, c_count;  // contribution range
   T alpha;
   int beta;              // 0 or 1
@@ -156,13 +156,21 @@ template <typename T>
 struct DiagTask {        // in-place Cholesky of an n x n tile (n <= kTile) and its inverse
   T* A;                  // tile, ld = lda; gets L (strict upper part zeroed)
   T* Li;                 // gets L^{-1}, ld = ldli
+  const T* d0;           // the front's diagonal before elimination, from the tile's first row (or null)
   int lda, ldli, n, node;
 };
+
+// Single precision: a pivot that kept less than kPivotLoss of its diagonal's
+// magnitude (fewer than about four significant bits after cancellation) is
+// reported like a non-positive one, so the factorization falls back to FP64
+// instead of carrying a pivot that rounding has decided.
+constexpr double kPivotLoss = 1.0 / (1 << 20);
 
 template <typename T>
 struct FrontTask {       // blocked Cholesky of D (m x m, ld m) and L^{-1} into Li (zero on entry)
   T* D;
   T* Li;
+  const T* d0;           // D's diagonal before elimination (or null)
   int m, node;
 };
 

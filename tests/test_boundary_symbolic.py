@@ -114,12 +114,13 @@ def test_footprint_is_positive_and_mixed_is_smaller():
 def test_tuning_round_trip_and_validation():
     P = sgf.Plan((16, 16, 16), 3, "7pt_fv_3d", 1, 8, 2, precision="mixed")
     assert P.tuning == {"gemv_min_elems": 4096, "gemv_max_elems": 32768, "front_small": 512, "tensor_cores": 1,
-                        "gemv_cols": 32}
-    P.tuning = {"gemv_min_elems": 1024, "front_small": 256, "tensor_cores": 0, "gemv_cols": 64}
+                        "gemv_cols": 32, "tc_min_dim": 64}
+    P.tuning = {"gemv_min_elems": 1024, "front_small": 256, "tensor_cores": 0, "gemv_cols": 64, "tc_min_dim": 128}
     assert P.tuning == {"gemv_min_elems": 1024, "gemv_max_elems": 32768, "front_small": 256, "tensor_cores": 0,
-                        "gemv_cols": 64}
+                        "gemv_cols": 64, "tc_min_dim": 128}
     for bad in ({"gemv_min_elems": 100}, {"gemv_min_elems": 65536, "gemv_max_elems": 4096},
-                {"front_small": 1024}, {"front_small": 32}, {"tensor_cores": 2}, {"gemv_cols": 48}):
+                {"front_small": 1024}, {"front_small": 32}, {"tensor_cores": 3}, {"tensor_cores": -1},
+                {"gemv_cols": 48}, {"tc_min_dim": 0}, {"tc_min_dim": 5000}):
         with pytest.raises(sgf.SGFError):
             P.tuning = bad
     assert P.tuning["front_small"] == 256      # unchanged by the rejected calls

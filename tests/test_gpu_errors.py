@@ -76,3 +76,25 @@ def test_mixed_falls_back_to_fp64_when_an_fp32_pivot_fails():
     assert abs(info["iterations"] - info64["iterations"]) <= 2
     F_ok = sgf.Factor(plan, _coeffs(cfg["coeffs"]))
     assert F_ok.precision == "mixed"      # an ordinary field stays in FP32
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sgf_sync_surfaces_a_nonfinite_apply(precision):
+    # an apply is enqueued and returns before the device runs it; a NaN in the
+    # host-made right-hand side reaches the output, and sgf_sync (through the
+    # C ABI) reports it once, then the flag is clear again
+    cfg = si.config("grf3d_16")
+    plan = sgf.Plan.from_config(cfg, precision=precision)
+    F = sgf.Factor(plan, _coeffs(cfg["coeffs"]))
+    assert F.sync() == 0
+    v = si.rhs(plan.n, 0)
+    y = F.apply(torch.tensor(v, dtype=torch.float64, device=DEV))
+    assert F.sync() == 0 and torch.isfinite(y).all()
+    v[plan.n // 3] = np.nan
+    y = F.apply(torch.tensor(v, dtype=torch.float64, device=DEV))
+    assert F.sync() == -3                       # SGF_ERR_NONFINITE
+    assert F.sync() == 0                        # read once, then cleared
+    F.apply_forward(torch.tensor(v, dtype=torch.float64, device=DEV))
+    assert F.sync() == -3                       # the multiply is checked too
+    y = F.apply(torch.tensor(si.rhs(plan.n, 1), dtype=torch.float64, device=DEV))
+    assert F.sync() == 0 and torch.isfinite(y).all()

@@ -6,7 +6,9 @@ shared by all calls.  This file is collected last so that a run stopping at
 the first failure has already run every other test.  It checks, through the
 C ABI, that two calls in a row give the regular sgf_pcg_solve's answer, that
 the scratch left by a previous call does not change the next result, and
-that a factor larger than the array is rejected.
+that a factor larger than the array is rejected.  The first call is made on a
+factor nothing has applied yet, and the library's allocation counter and the
+device pool's used bytes must not move across the calls (sgf_memory_stats).
 """
 import ctypes as C
 
@@ -27,9 +29,10 @@ from paper_1907_03406_gb300 import _lib  # noqa: E402
 DEV = torch.device("cuda:0")
 
 
-def _noalloc(F, b, rtol=1e-10, maxit=500):
+def _noalloc(F, b, rtol=1e-10, maxit=500, x=None):
     lib = _lib.load()
-    x = torch.full_like(b, float("nan"))
+    if x is None:
+        x = torch.full_like(b, float("nan"))
     info = _lib.sgf_solve_info()
     rc = lib.sgf_pcg_solve_noalloc(F.handle, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()),
                                    float(rtol), int(maxit),
@@ -45,10 +48,19 @@ def test_noalloc_matches_regular_pcg_two_calls(precision):
     F = sgf.Factor(plan, coeffs)
     b1 = torch.tensor(si.rhs(plan.n, 0), dtype=torch.float64, device=DEV)
     b2 = torch.tensor(si.rhs(plan.n, 1), dtype=torch.float64, device=DEV)
-    for b in (b1, b2):          # two calls in a row, different right-hand sides
-        x_ref, info_ref = F.pcg(b, rtol=1e-10, maxit=500)
-        rc, x, info = _noalloc(F, b)
+    results = []
+    xs = [torch.full_like(b1, float("nan")) for _ in range(2)]
+    torch.cuda.synchronize()
+    for b, x0 in zip((b1, b2), xs):   # two calls in a row on a fresh factor, nothing else in between
+        before = sgf.memory_stats()
+        rc, x, info = _noalloc(F, b, x=x0)
+        after = sgf.memory_stats()
         assert rc == 0, sgf.SGFError(rc, "noalloc")
+        assert after["alloc_events"] == before["alloc_events"]
+        assert after["pool_used_bytes"] == before["pool_used_bytes"]
+        results.append((x, info))
+    for b, (x, info) in zip((b1, b2), results):   # the regular solve (which allocates) after
+        x_ref, info_ref = F.pcg(b, rtol=1e-10, maxit=500)
         assert info.iterations == info_ref["iterations"]
         assert info.rel_residual <= 1e-10
         err = torch.linalg.norm(x - x_ref).item() / torch.linalg.norm(x_ref).item()
