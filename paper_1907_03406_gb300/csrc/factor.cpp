@@ -423,8 +423,7 @@ struct Front {
 // Blocked right-looking Cholesky of D with the triangular solves of the panel
 // and of the identity (giving L^{-1}), batched over all fronts.
 template <typename T>
-void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level,
-                std::vector<void*>& work) {
+void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, DevStatus* st, int level) {
   // Small fronts without a panel: one CTA does the whole sweep.  Beyond
   // front_small the tile sweep spread over many CTAs wins (one CTA pays a
   // memory latency per tile product), and so it does for fronts above
@@ -434,35 +433,11 @@ void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, Dev
   for (const auto& f : Fall)
     if (f.s == 0 && f.m <= small_max) ++nfit;
   const int cut = nfit >= kFrontBatchMin ? small_max : std::min(kFrontTiny, small_max);
-  // single precision: every front's diagonal before elimination, for the
-  // pivot-significance check (kPivotLoss)
-  std::vector<const T*> d0(Fall.size(), nullptr);
-  if (std::is_same<T, float>::value && !Fall.empty()) {
-    size_t tot = 0;
-    for (const auto& f : Fall) tot += f.m;
-    T* dsave = (T*)dev_malloc_async(sizeof(T) * std::max<size_t>(tot, 1), s);
-    work.push_back(dsave);
-    CopyList<T, T> cd;
-    size_t o = 0;
-    for (size_t k = 0; k < Fall.size(); ++k) {
-      const auto& f = Fall[k];
-      if (f.m > 0) cd.add(f.D, f.m + 1, dsave + o, 1, 1, f.m, kCopy);   // the diagonal: stride m + 1
-      d0[k] = dsave + o;
-      o += f.m;
-    }
-    cd.emit(b, s);
-  }
   std::vector<FrontTask<T>> small;
   std::vector<Front<T>> F;
-  std::vector<const T*> Fd0;
-  for (size_t k = 0; k < Fall.size(); ++k) {
-    const auto& f = Fall[k];
-    if (f.s == 0 && f.m <= cut) {
-      small.push_back({f.D, f.Li, d0[k], f.m, f.node});
-    } else {
-      F.push_back(f);
-      Fd0.push_back(d0[k]);
-    }
+  for (const auto& f : Fall) {
+    if (f.s == 0 && f.m <= cut) small.push_back({f.D, f.Li, f.m, f.node});
+    else F.push_back(f);
   }
   if (!small.empty()) {
     const size_t of = b.push(small);
@@ -479,14 +454,13 @@ void run_fronts(const std::vector<Front<T>>& Fall, Batch& b, cudaStream_t s, Dev
   for (int k = 0; k < kmax; ++k) {
     std::vector<DiagTask<T>> dt;
     GemmList<T> panel, update;
-    for (size_t fi = 0; fi < F.size(); ++fi) {
-      const auto& f = F[fi];
+    for (const auto& f : F) {
       const int m = f.m, nt = (m + kTile - 1) / kTile;
       if (k >= nt) continue;
       const int r0 = k * kTile, nk = std::min(kTile, m - r0), r1 = r0 + nk;
       T* Dkk = f.D + r0 + (size_t)r0 * m;
       T* Likk = f.Li + r0 + (size_t)r0 * m;
-      dt.push_back({Dkk, Likk, Fd0[fi] ? Fd0[fi] + r0 : nullptr, m, m, nk, f.node});
+      dt.push_back({Dkk, Likk, m, m, nk, f.node});
       // panel: L_ik = A_ik L_kk^{-T} (i > k); X_k = L_kk^{-1} B_k for the RHS
       for (int ri = r1; ri < m; ri += kTile) {
         const int ni = std::min(kTile, m - ri);
@@ -1079,7 +1053,7 @@ class FactorImpl final : public FactorBase {
         Ltop_ = Dg;
         Litop_ = dalloc<T>(keep_, (size_t)mtop_ * mtop_, s);
         std::vector<Front<T>> F = {{Dg, mtop_, nullptr, 0, Litop_, 0}};
-        if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl, work_);
+        if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl);
         b.run(s);
         if (mtop_ > 0) {   // stream ordered after the top factor
           CopyList<T, T> cm;
@@ -1128,7 +1102,7 @@ class FactorImpl final : public FactorBase {
         for (int k = lay.up_ptr[i]; k < lay.up_ptr[i + 1]; ++k) r.nb.push_back({lay.up_nb[k], lay.up_col[k]});
         rec.in.push_back(r);
       }
-      run_fronts<T>(F, b, s, st_, lvl, work_);
+      run_fronts<T>(F, b, s, st_, lvl);
       b.run(s);
       trace(s, lvl, "interior fronts");
       {
@@ -1287,7 +1261,7 @@ class FactorImpl final : public FactorBase {
       {
         std::vector<Front<T>> FB;
         for (int e = 0; e < ne; ++e) FB.push_back({Dw + o_mm[e], m[E[e]], nullptr, 0, LiB + o_mm[e], E[e]});
-        run_fronts<T>(FB, b, s, st_, lvl, work_);
+        run_fronts<T>(FB, b, s, st_, lvl);
         {
           // M^_B,nbrs = L_B^{-1} A_B,nbrs (Eq. (compr-scale))
           GemmList<T> gm;

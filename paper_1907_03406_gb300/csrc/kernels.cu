@@ -220,13 +220,15 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 // One CTA per kTileTC x kTileTC output tile (M, N <= 128); the contributions'
 // K ranges are walked in chunks of kTcKC.  Nine warps, specialized, with no
 // CTA barrier in the main loop:
-//  * warps 0-3 (producers) load their share of chunk c + 2 from global memory
-//    into registers, then split the values of chunk c (loaded two chunks
-//    earlier) into NPART TF32 parts (each rounded to nearest: v = p0 + p1
-//    [+ p2] up to the last part's rounding) and store them K-major in the
-//    no-swizzle canonical layout (core matrices of 8 rows x 16 bytes, 128
-//    bytes apart along K, kTcKC / 4 * 128 bytes apart along rows) into stage
-//    c mod kTcStages, then arrive on the stage's "full" mbarrier;
+//  * warps 0-3 (producers) copy chunk c + 3 from global memory into a raw
+//    shared-memory ring by 4-byte cp.async (coalesced whichever index of an
+//    operand is contiguous), then, once chunk c has landed for all of them
+//    (a barrier among the producers only), split their rows of it into
+//    NPART TF32 parts (each rounded to nearest: v = p0 + p1 [+ p2] up to the
+//    last part's rounding) and store them K-major in the no-swizzle
+//    canonical layout (core matrices of 8 rows x 16 bytes, 128 bytes apart
+//    along K, kTcKC / 4 * 128 bytes apart along rows) into operand stage
+//    c mod kStages, then arrive on the stage's "full" mbarrier;
 //  * one thread of warp 4 waits for "full", issues per 8-wide K step the
 //    split products (NPART = 2: p0q0 + p0q1 + p1q0, the 3xTF32 scheme;
 //    NPART = 3: also p0q2 + p1q1 + p2q0) as tcgen05.mma kind::tf32 (M = N =
@@ -244,16 +246,19 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 // flight, poisons the tile with NaN (reported downstream as a non-finite
 // factor) instead of hanging, and the tensor memory is released on every path.
 constexpr int kTcKC = 16;
-constexpr int kTcStages = 4;
 constexpr int kTcFlush = 2;                  // chunks per tensor-memory partial sum
 constexpr int kTcThreads = 9 * 32;
 constexpr int kTcPartA = kTileTC * kTcKC;    // floats of one operand part per stage
+constexpr int kTcRawPitch = 20;              // raw chunk rows: 16 values + pad (16-byte aligned, few conflicts)
+constexpr int kTcRawStage = 2 * kTileTC * kTcRawPitch;   // floats: op(A) rows then op(B)^T rows
+constexpr int kTcRaw = 4;                    // raw ring depth: kTcRaw - 1 chunks in flight
 constexpr int kTcWaitIters = 1 << 22;
 
 template <int NPART>
 struct TcCfg {
+  static constexpr int kStages = NPART == 2 ? 4 : 2;    // split operand stages
   static constexpr int kStage = 2 * NPART * kTcPartA;   // A and B parts
-  static constexpr size_t kSmem = sizeof(float) * (size_t)kTcStages * kStage;
+  static constexpr size_t kSmem = sizeof(float) * ((size_t)kStages * kStage + (size_t)kTcRaw * kTcRawStage);
 };
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
@@ -302,67 +307,76 @@ __device__ __forceinline__ void tc_cursor_next(TcCursor& u, const GemmContrib<fl
   }
 }
 
-// Producer thread p (0..127) loads 16 values of op(A) and 16 of op(B)^T for
-// one chunk (zero outside the task / contribution).  Non-transposed A (rows
-// contiguous): row p, k = 0..15.  Transposed A (k contiguous): k group p mod 4
-// (four consecutive k), rows p / 4 + 32 j.  op(B)^T likewise with B^T playing
-// the role of A.
-__device__ __forceinline__ void tc_load(const GemmContrib<float>& cb, int k0, int M, int N, int p, float (&ra)[16],
-                                        float (&rb)[16]) {
+__device__ __forceinline__ void tc_cp4(uint32_t dst, const float* src, bool ok) {
+  // 4-byte asynchronous copy; zero-filled (nothing read) when !ok
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+
+// Producer thread p (0..127) copies its share of one chunk into a raw stage
+// (row r of op(A) at r * kTcRawPitch, row j of op(B)^T after the 128 A rows),
+// coalesced for either storage order: rows contiguous in memory: thread p
+// takes row p, k = 0..15 (a warp reads 32 consecutive rows per k); k
+// contiguous: thread p takes k = p mod 16 of rows p / 16 + 8 j (a warp reads
+// 64 contiguous bytes of two rows).  Positions outside the task (rows >= M /
+// N, k beyond the contribution) are zero-filled.
+__device__ __forceinline__ void tc_copy(const GemmContrib<float>& cb, int k0, int M, int N, int p, uint32_t sraw) {
   const int kc = min(kTcKC, cb.K - k0);
-  if (!(cb.flags & kTransA)) {
-    const bool ok = p < M;
+  if (!(cb.flags & kTransA)) {   // op(A) = A, M x K column-major: rows contiguous
     const float* a = cb.A + p + (size_t)k0 * cb.lda;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) ra[k] = (ok && k < kc) ? __ldg(a + (size_t)k * cb.lda) : 0.f;
-  } else {
-    const int kq = p & 3;
+    for (int k = 0; k < 16; ++k)
+      tc_cp4(sraw + 4u * (p * kTcRawPitch + k), p < M && k < kc ? a + (size_t)k * cb.lda : cb.A, p < M && k < kc);
+  } else {                       // op(A) = A^T, A is K x M: k contiguous
+    const int k = p & 15;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int i = (p >> 2) + 32 * j;
-      const float* a = cb.A + k0 + 4 * kq + (size_t)i * cb.lda;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) ra[4 * j + e] = (i < M && 4 * kq + e < kc) ? __ldg(a + e) : 0.f;
+    for (int j = 0; j < 16; ++j) {
+      const int i = (p >> 4) + 8 * j;
+      const bool ok = i < M && k < kc;
+      tc_cp4(sraw + 4u * (i * kTcRawPitch + k), ok ? cb.A + k0 + k + (size_t)i * cb.lda : cb.A, ok);
     }
   }
-  if (cb.flags & kTransB) {   // op(B)^T = B, N x K, rows j contiguous
-    const bool ok = p < N;
+  const uint32_t sb = sraw + 4u * kTileTC * kTcRawPitch;
+  if (cb.flags & kTransB) {      // op(B)^T = B, N x K: rows j contiguous
     const float* b = cb.B + p + (size_t)k0 * cb.ldb;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) rb[k] = (ok && k < kc) ? __ldg(b + (size_t)k * cb.ldb) : 0.f;
-  } else {                    // op(B) = B, K x N column-major: k contiguous
-    const int kq = p & 3;
+    for (int k = 0; k < 16; ++k)
+      tc_cp4(sb + 4u * (p * kTcRawPitch + k), p < N && k < kc ? b + (size_t)k * cb.ldb : cb.B, p < N && k < kc);
+  } else {                       // op(B) = B, K x N column-major: k contiguous
+    const int k = p & 15;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int i = (p >> 2) + 32 * j;
-      const float* b = cb.B + k0 + 4 * kq + (size_t)i * cb.ldb;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) rb[4 * j + e] = (i < N && 4 * kq + e < kc) ? __ldg(b + e) : 0.f;
+    for (int j = 0; j < 16; ++j) {
+      const int i = (p >> 4) + 8 * j;
+      const bool ok = i < N && k < kc;
+      tc_cp4(sb + 4u * (i * kTcRawPitch + k), ok ? cb.B + k0 + k + (size_t)i * cb.ldb : cb.B, ok);
     }
   }
 }
 
-// split 16 values of one operand into NPART parts and store them; rowk: the
-// values are row p, k = 0..15; else rows p / 4 + 32 q, k = 4 (p mod 4) + e
+// Producer thread p splits row p of op(A) and of op(B)^T from a raw stage
+// into NPART TF32 parts and stores them in the canonical K-major layout
 template <int NPART>
-__device__ __forceinline__ void tc_store(float* base, bool rowk, int p, const float (&r)[16]) {
+__device__ __forceinline__ void tc_split(const float* raw, float* base, int p) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int row, kq;
-    if (rowk) { row = p; kq = q; } else { row = (p >> 2) + 32 * q; kq = p & 3; }
-    const int off = (row >> 3) * (kTcKC / 4) * 32 + kq * 32 + (row & 7) * 4;   // floats
-    float v[4] = {r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]};
+  for (int mat = 0; mat < 2; ++mat) {
+    const float* r = raw + (mat * kTileTC + p) * kTcRawPitch;
+    float* dst = base + mat * NPART * kTcPartA;
 #pragma unroll
-    for (int part = 0; part < NPART; ++part) {
-      float4 o;
-      float* po = reinterpret_cast<float*>(&o);
+    for (int kq = 0; kq < kTcKC / 4; ++kq) {
+      const float4 in = *reinterpret_cast<const float4*>(r + 4 * kq);
+      float v[4] = {in.x, in.y, in.z, in.w};
+      const int off = (p >> 3) * (kTcKC / 4) * 32 + kq * 32 + (p & 7) * 4;   // floats
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float h = tf32_rna(v[e]);
-        po[e] = h;
-        v[e] -= h;
+      for (int part = 0; part < NPART; ++part) {
+        float4 o;
+        float* po = reinterpret_cast<float*>(&o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float h = tf32_rna(v[e]);
+          po[e] = h;
+          v[e] -= h;
+        }
+        *reinterpret_cast<float4*>(dst + part * kTcPartA + off) = o;
       }
-      *reinterpret_cast<float4*>(base + part * kTcPartA + off) = o;
     }
   }
 }
@@ -382,20 +396,22 @@ template <int NPART>
 __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>* __restrict__ tasks,
                                                            const GemmContrib<float>* __restrict__ cons) {
   using Cfg = TcCfg<NPART>;
+  constexpr int kStages = Cfg::kStages;
   const GemmTask<float> tk = tasks[blockIdx.x];
   extern __shared__ __align__(1024) unsigned char tc_smraw[];
-  float* stg = reinterpret_cast<float*>(tc_smraw);   // kTcStages x [A parts | B parts]
+  float* stg = reinterpret_cast<float*>(tc_smraw);   // kStages x [A parts | B parts]
+  float* raw = stg + kStages * Cfg::kStage;           // kTcRaw x [A rows | B rows]
   // full[s], empty[s], acc_full[2], acc_empty[2], done
-  __shared__ __align__(8) uint64_t mbar[2 * kTcStages + 5];
+  __shared__ __align__(8) uint64_t mbar[2 * kStages + 5];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
   auto full = [&](int st) { return mb + 8u * st; };
-  auto empty = [&](int st) { return mb + 8u * (kTcStages + st); };
-  auto acc_full = [&](int b) { return mb + 8u * (2 * kTcStages + b); };
-  auto acc_empty = [&](int b) { return mb + 8u * (2 * kTcStages + 2 + b); };
-  const uint32_t done = mb + 8u * (2 * kTcStages + 4);
+  auto empty = [&](int st) { return mb + 8u * (kStages + st); };
+  auto acc_full = [&](int b) { return mb + 8u * (2 * kStages + b); };
+  auto acc_empty = [&](int b) { return mb + 8u * (2 * kStages + 2 + b); };
+  const uint32_t done = mb + 8u * (2 * kStages + 4);
   if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
@@ -404,7 +420,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int st = 0; st < kTcStages; ++st) {
+    for (int st = 0; st < kStages; ++st) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full(st)), "r"(128) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(st)) : "memory");
     }
@@ -426,41 +442,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   const int ngrp = (nch + kTcFlush - 1) / kTcFlush;
 
   if (warp < 4) {
-    // ---- producers
+    // ---- producers: chunk c is copied into raw stage c mod kTcRaw kTcRaw - 1
+    // chunks ahead; once every producer's copies of it have landed (a
+    // producer-only barrier) each thread splits its rows into the operand
+    // stage c mod kStages
     const int p = tid;
+    const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(raw);
     TcCursor ld{tk.c_begin, 0};
     while (ld.c < cend && cons[ld.c].K <= 0) ++ld.c;
-    TcCursor sp = ld;   // the chunk being stored (its contribution's layout flags)
-    float ra[3][16], rb[3][16];
-    auto load_next = [&](float (&a)[16], float (&b)[16]) {
-      const GemmContrib<float> cb = cons[ld.c];
-      tc_load(cb, ld.k0, M, N, p, a, b);
-      tc_cursor_next(ld, cons, cend);
+    int issued = 0;
+    auto issue = [&]() {   // one copy group per call (empty past the last chunk)
+      if (issued < nch) {
+        tc_copy(cons[ld.c], ld.k0, M, N, p, sraw + 4u * (issued % kTcRaw) * kTcRawStage);
+        tc_cursor_next(ld, cons, cend);
+      }
+      ++issued;
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    if (nch > 0) load_next(ra[0], rb[0]);
-    if (nch > 1) load_next(ra[1], rb[1]);
+    for (int k = 0; k < kTcRaw - 1; ++k) issue();
     bool bad = false;
-    for (int c0 = 0; c0 < nch && !bad; c0 += 3) {
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int c = c0 + u;
-        if (c < nch && !bad) {
-          if (c + 2 < nch) load_next(ra[(u + 2) % 3], rb[(u + 2) % 3]);
-          const int st = c % kTcStages;
-          if (c >= kTcStages && !tc_wait(empty(st), (uint32_t)(((c / kTcStages) + 1) & 1))) {
-            bad = true;
-            break;
-          }
-          const int fl = cons[sp.c].flags;
-          float* base = stg + st * Cfg::kStage;
-          tc_store<NPART>(base, !(fl & kTransA), p, ra[u]);
-          tc_store<NPART>(base + NPART * kTcPartA, (fl & kTransB) != 0, p, rb[u]);
-          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full(st)) : "memory");
-          tc_cursor_next(sp, cons, cend);
-        }
+    for (int c = 0; c < nch; ++c) {
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcRaw - 2) : "memory");
+      asm volatile("bar.sync 1, 128;\n" ::: "memory");   // chunk c landed everywhere; stage c - 1 read
+      issue();                                              // chunk c + kTcRaw - 1 into stage (c - 1) mod kTcRaw
+      // a producer whose wait gives up keeps walking the loop (so the
+      // producer barrier above never waits for it in vain) without storing
+      const int st = c % kStages;
+      if (!bad && c >= kStages && !tc_wait(empty(st), (uint32_t)(((c / kStages) + 1) & 1))) bad = true;
+      if (!bad) {
+        tc_split<NPART>(raw + (c % kTcRaw) * kTcRawStage, stg + st * Cfg::kStage, p);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full(st)) : "memory");
       }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (bad) atomicExch(&s_bad, 1);
   } else if (warp == 4) {
     // ---- MMA issue (one thread)
@@ -476,8 +491,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
         const uint32_t dacc = tmem + (uint32_t)(b * kTileTC);
         const int c1 = min(nch, (g + 1) * kTcFlush);
         for (int c = g * kTcFlush; c < c1; ++c) {
-          const int st = c % kTcStages;
-          if (!tc_wait(full(st), (uint32_t)((c / kTcStages) & 1))) {
+          const int st = c % kStages;
+          if (!tc_wait(full(st), (uint32_t)((c / kStages) & 1))) {
             bad = true;
             break;
           }
@@ -595,7 +610,7 @@ constexpr int kPitch = kTile + 1;
 // is a forward substitution per column of V, each owned by four lanes of one
 // warp, so its row steps need only warp synchronisation.
 template <typename T>
-__device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V, const T* d0) {
+__device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V) {
   __shared__ int bad;
   __shared__ T dinv[kTile];   // d_j^{-1/2}
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
@@ -608,10 +623,9 @@ __device__ int diag_tile(T* A, int lda, T* Li, int ldli, int n, T* S, T* V, cons
   int mybad = 0;
   for (int j = 0; j < n; ++j) {
     T d = S[j * kPitch + j];
-    const bool lost = sizeof(T) == 4 && d0 && d <= T(kPivotLoss) * d0[j];
-    if (!(d > T(0)) || !isfinite(d) || lost) {
+    if (!(d > T(0)) || !isfinite(d)) {
       mybad = isfinite(d) ? 1 : 2;
-      if (!(d > T(0)) || !isfinite(d)) d = T(1);
+      d = T(1);
     }
     const T rd = T(1) / d;
     // trailing lower triangle, 16 x 16 thread grid; column j itself is read only
@@ -661,7 +675,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagTask<T>* __restrict
   extern __shared__ __align__(16) unsigned char smraw[];
   T* S = reinterpret_cast<T*>(smraw);
   T* V = S + kTile * kPitch;
-  const int bad = diag_tile<T>(tk.A, tk.lda, tk.Li, tk.ldli, tk.n, S, V, tk.d0);
+  const int bad = diag_tile<T>(tk.A, tk.lda, tk.Li, tk.ldli, tk.n, S, V);
   if (threadIdx.x == 0 && bad) report(st, bad == 1 ? SGF_ERR_NOT_SPD : SGF_ERR_NONFINITE, level, tk.node);
 }
 
@@ -839,7 +853,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_front(const FrontTask<T>* __res
   for (int k = 0; k < nt; ++k) {
     const int r0 = k * kTile, nk = min(kTile, m - r0), r1 = r0 + nk;
     T* Likk = Li + r0 + (size_t)r0 * m;
-    const int b = diag_tile<T>(D + r0 + (size_t)r0 * m, m, Likk, m, nk, S, V, tk.d0 ? tk.d0 + r0 : nullptr);
+    const int b = diag_tile<T>(D + r0 + (size_t)r0 * m, m, Likk, m, nk, S, V);
     if (b && !bad) bad = b;
     for (int ri = r1; ri < m; ri += kTile) {
       T* C = D + ri + (size_t)r0 * m;
@@ -1837,7 +1851,6 @@ void launch_diag(const DiagTask<T>* tasks, int n, DevStatus* st, int level, cuda
       if (tasks[i].n > kTile || tasks[i].n < 1) check_range(nullptr, 1, "diag tile shape");
       check_block(tasks[i].A, tasks[i].n, tasks[i].n, tasks[i].lda, sizeof(T), "diag A");
       check_block(tasks[i].Li, tasks[i].n, tasks[i].n, tasks[i].ldli, sizeof(T), "diag Li");
-      if (tasks[i].d0) check_range(tasks[i].d0, sizeof(T) * tasks[i].n, "diag diagonal");
     }
     return;
   }
@@ -1858,7 +1871,6 @@ void launch_front(const FrontTask<T>* tasks, int n, DevStatus* st, int level, cu
     for (int i = 0; i < n; ++i) {
       check_block(tasks[i].D, tasks[i].m, tasks[i].m, tasks[i].m, sizeof(T), "front D");
       check_block(tasks[i].Li, tasks[i].m, tasks[i].m, tasks[i].m, sizeof(T), "front Li");
-      if (tasks[i].d0) check_range(tasks[i].d0, sizeof(T) * tasks[i].m, "front diagonal");
     }
     return;
   }

@@ -156,21 +156,13 @@ template <typename T>
 struct DiagTask {        // in-place Cholesky of an n x n tile (n <= kTile) and its inverse
   T* A;                  // tile, ld = lda; gets L (strict upper part zeroed)
   T* Li;                 // gets L^{-1}, ld = ldli
-  const T* d0;           // the front's diagonal before elimination, from the tile's first row (or null)
   int lda, ldli, n, node;
 };
-
-// Single precision: a pivot that kept less than kPivotLoss of its diagonal's
-// magnitude (fewer than about four significant bits after cancellation) is
-// reported like a non-positive one, so the factorization falls back to FP64
-// instead of carrying a pivot that rounding has decided.
-constexpr double kPivotLoss = 1.0 / (1 << 20);
 
 template <typename T>
 struct FrontTask {       // blocked Cholesky of D (m x m, ld m) and L^{-1} into Li (zero on entry)
   T* D;
   T* Li;
-  const T* d0;           // D's diagonal before elimination (or null)
   int m, node;
 };
 

@@ -55,14 +55,14 @@ def test_maxit_reports_no_convergence():
 
 
 def test_mixed_falls_back_to_fp64_when_an_fp32_pivot_fails():
-    # an SPD field with a 1e12 inclusion: the FP32 Cholesky of the blocks
-    # around it loses the inclusion's weak coupling to rounding (relative
-    # 1e-12 < eps32) and meets a non-positive pivot, FP64 does not; the mixed
-    # request is refactored in FP64 and solves as well as an FP64 plan (at this
-    # contrast the attainable true residual is ~eps64 cond(A) ~ 1e-4, for both)
+    # an SPD field with a 1e39 inclusion: its diagonal entries (6e39) exceed
+    # the single-precision range, so the FP32 factorization meets a
+    # non-finite pivot while FP64 does not; the mixed request is refactored
+    # in FP64 and runs exactly as an FP64 plan (at this contrast neither
+    # reaches 1e-10: the attainable residual is ~eps64 cond(A))
     cfg = si.config("grf3d_16")
     k = np.ones_like(cfg["coeffs"])
-    k[2:6, 2:6, 2:6] = 1e12
+    k[2:6, 2:6, 2:6] = 1e39
     b = torch.tensor(si.rhs(int(np.prod(cfg["n"])), 0), dtype=torch.float64, device=DEV)
     plan64 = sgf.Plan.from_config(cfg, precision="fp64")
     F64 = sgf.Factor(plan64, _coeffs(k))
