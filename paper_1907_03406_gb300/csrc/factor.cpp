@@ -42,8 +42,10 @@
 #include <cstring>
 #include <initializer_list>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
+#include <string>
 #include <type_traits>
 
 #include "devmem.h"
@@ -341,7 +343,25 @@ struct GemmList {
       work(t, c, fl, by);
       const size_t ot = b.push(t);
       const int n = (int)t.size(), parts = tcmode == 1 ? 2 : 3;
+      // launch-log description: tiles, full 128 x 128 tiles, the K sums
+      std::shared_ptr<std::string> note;
+      if (prof_logging()) {
+        double ksum = 0, kmax = 0, full = 0, cmax = 0;
+        for (const auto& g : t) {
+          double k = 0;
+          for (int q = g.c_begin; q < g.c_begin + g.c_count; ++q) k += c[q].K;
+          ksum += k;
+          kmax = std::max(kmax, k);
+          cmax = std::max(cmax, (double)g.c_count);
+          full += g.M == kTileTC && g.N == kTileTC;
+        }
+        char buf[192];
+        std::snprintf(buf, sizeof buf, "tc tiles %d full %.0f kavg %.0f kmax %.0f cmax %.0f", n, full, ksum / n, kmax,
+                      cmax);
+        note = std::make_shared<std::string>(buf);
+      }
       b.launches.push_back([=](const char* d) {
+        if (note) prof_note(note->c_str());
         prof_work(fl, by);
         if constexpr (std::is_same<T, float>::value)
           launch_gemm_tc((const GemmTask<float>*)(d + ot), (const GemmContrib<float>*)(d + oc), n, parts, s);
@@ -575,6 +595,7 @@ struct GemvList {
   std::vector<GemvContrib<T>> c;
   bool trans = false;
   int nr = 1;  // interleaved right-hand sides
+  std::string tag;   // phase and level, for the launch log
   // op T chunk width: the tuning's in single precision, kGemvCols in double
   const int cols = std::is_same<T, float>::value ? active_tuning().gemv_cols : kGemvCols;
   explicit GemvList(int nr_ = 1) : nr(nr_) {}
@@ -758,7 +779,25 @@ struct GemvList {
     int max_m = 1;
     for (const auto& h : ct) max_m = std::max(max_m, h.M);
     P.acct.push_back({tr ? P_GEMV_T : P_GEMV_N, fl * r, by});
+    // launch-log description: phase, CTA / warp tasks, the largest task's
+    // elements and contributions, the split budget
+    std::shared_ptr<std::string> note;
+    if (prof_logging()) {
+      double emax = 0;
+      int cmax = 0, mmax = 0, nsp = 0;
+      for (const auto& h : tasks) {
+        emax = std::max(emax, (double)h.M * (h.k_hi - h.k_lo));
+        cmax = std::max(cmax, h.c_count);
+        mmax = std::max(mmax, h.M);
+        nsp += h.nsplit > 1;
+      }
+      char buf[256];
+      std::snprintf(buf, sizeof buf, "%s cta %d warp %d split %d el %.3g emax %.0f cmax %d mmax %d budget %.0f",
+                    tag.c_str(), n, nw, nsp, el_all, emax, cmax, mmax, budget);
+      note = std::make_shared<std::string>(buf);
+    }
     P.ops.push_back([=](const char* d, cudaStream_t st) {
+      if (note) prof_note(note->c_str());
       prof_work(fl * r, by);
       const GemvTask<T>* cta = (const GemvTask<T>*)(d + ot);
       const GemvTask<T>* wtk = nw > 0 ? (const GemvTask<T>*)(d + ow) : nullptr;
@@ -1655,6 +1694,10 @@ class FactorImpl final : public FactorBase {
     // mirrored upper triangle, W^T x and L^{-T} x through the columns
     GemvList<T> f1(nr), f2(nr), f3(nr), f4(nr);
     f1.trans = f2.trans = f3.trans = f4.trans = true;
+    f1.tag = "L" + std::to_string(t) + ".f1";
+    f2.tag = "L" + std::to_string(t) + ".f2";
+    f3.tag = "L" + std::to_string(t) + ".f3";
+    f4.tag = "L" + std::to_string(t) + ".f4";
     for (const auto& r : R.in)
       f1.add(w + nr * lay.vec_off[r.node], r.m, 0,
              {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1), true}});
@@ -1690,6 +1733,8 @@ class FactorImpl final : public FactorBase {
     T* w = vtop_ + (size_t)mtop_ * nr;
     GemvList<T> a(nr), bt(nr);
     a.trans = bt.trans = true;
+    a.tag = "top.a";
+    bt.tag = "top.b";
     a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1), true}});
     bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
     a.emit(P, s);
@@ -1711,6 +1756,10 @@ class FactorImpl final : public FactorBase {
     veccopy(P, vc, vn, v);
     GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
     b2.trans = b3.trans = b4.trans = true;
+    b1.tag = "L" + std::to_string(t) + ".b1";
+    b2.tag = "L" + std::to_string(t) + ".b2";
+    b3.tag = "L" + std::to_string(t) + ".b3";
+    b4.tag = "L" + std::to_string(t) + ".b4";
     for (const auto& c : R.sep) {
       if (!c.comp) continue;
       b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});

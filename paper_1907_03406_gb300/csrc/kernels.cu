@@ -218,18 +218,20 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 // tensor-core tile GEMM (FP32 operands as split TF32 products, FP32 accumulation)
 // ---------------------------------------------------------------------------
 // One CTA per kTileTC x kTileTC output tile (M, N <= 128); the contributions'
-// K ranges are walked in chunks of kTcKC.  Nine warps, specialized, with no
-// CTA barrier in the main loop:
-//  * warps 0-3 (producers) copy chunk c + 3 from global memory into a raw
-//    shared-memory ring by 4-byte cp.async (coalesced whichever index of an
-//    operand is contiguous), then, once chunk c has landed for all of them
-//    (a barrier among the producers only), split their rows of it into
-//    NPART TF32 parts (each rounded to nearest: v = p0 + p1 [+ p2] up to the
-//    last part's rounding) and store them K-major in the no-swizzle
-//    canonical layout (core matrices of 8 rows x 16 bytes, 128 bytes apart
-//    along K, kTcKC / 4 * 128 bytes apart along rows) into operand stage
-//    c mod kStages, then arrive on the stage's "full" mbarrier;
-//  * one thread of warp 4 waits for "full", issues per 8-wide K step the
+// K ranges are walked in chunks of kTcKC.  Seventeen warps, specialized, with
+// no CTA barrier in the main loop:
+//  * warps 0-7 (producers: warps 0-3 for op(A), 4-7 for op(B)^T, thread q of
+//    a group owning row q of its operand) copy chunk c + 3 from global memory
+//    into a raw shared-memory ring by 4-byte cp.async (coalesced whichever
+//    index of an operand is contiguous), then, once chunk c has landed for
+//    all of them (a barrier among the producers only), split their rows of it
+//    into NPART TF32 parts (each the remainder so far rounded to nearest
+//    TF32, so v = p0 + p1 [+ p2] up to the last part's rounding) and store
+//    them K-major in the no-swizzle canonical layout
+//    (core matrices of 8 rows x 16 bytes, 128 bytes apart along K, kTcKC / 4
+//    * 128 bytes apart along rows) into operand stage c mod kStages, then
+//    arrive on the stage's "full" mbarrier;
+//  * one thread of warp 8 waits for "full", issues per 8-wide K step the
 //    split products (NPART = 2: p0q0 + p0q1 + p1q0, the 3xTF32 scheme;
 //    NPART = 3: also p0q2 + p1q1 + p2q0) as tcgen05.mma kind::tf32 (M = N =
 //    128) and commits to the stage's "empty" mbarrier so the producers refill
@@ -237,9 +239,10 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 //    linearly with the number of additions, so a partial sum only covers
 //    kTcFlush chunks: groups of chunks alternate between two 128-column
 //    tensor-memory accumulators ("acc full" commits, "acc empty" arrivals);
-//  * warps 5-8 (accumulators, tensor-memory lane quadrants 1, 2, 3, 0) read
-//    every finished partial with tcgen05.ld and add it to FP32 registers
-//    (round to nearest), then write C = beta C + alpha sum.
+//  * warps 9-16 (accumulators; warp w reads tensor-memory lanes 32 (w mod 4)
+//    .. + 31, columns 64 ((w - 9) / 4) .. + 63) read every finished partial
+//    with tcgen05.ld and add it to FP32 registers (round to nearest), then
+//    write C = beta C + alpha sum.
 // Rows of an operand beyond the task's M / N and K positions beyond a
 // contribution's K are stored as zeros.  Every mbarrier wait is bounded; a
 // wait that gives up stops the pipeline, waits (bounded) for the products in
@@ -247,7 +250,13 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 // factor) instead of hanging, and the tensor memory is released on every path.
 constexpr int kTcKC = 16;
 constexpr int kTcFlush = 2;                  // chunks per tensor-memory partial sum
-constexpr int kTcThreads = 9 * 32;
+constexpr int kTcProdWarps = 8;              // warps 0-7
+constexpr int kTcProd = kTcProdWarps * 32;
+constexpr int kTcMmaWarp = 8;
+constexpr int kTcAccWarp0 = 9;               // warps 9-16
+constexpr int kTcAccWarps = 8;
+constexpr int kTcAccCols = kTileTC * 4 / kTcAccWarps;   // columns per accumulator warp
+constexpr int kTcThreads = (kTcAccWarp0 + kTcAccWarps) * 32;
 constexpr int kTcPartA = kTileTC * kTcKC;    // floats of one operand part per stage
 constexpr int kTcRawPitch = 20;              // raw chunk rows: 16 values + pad (16-byte aligned, few conflicts)
 constexpr int kTcRawStage = 2 * kTileTC * kTcRawPitch;   // floats: op(A) rows then op(B)^T rows
@@ -286,24 +295,32 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ float tf32_rna(float v) {
+// v rounded to TF32 (nearest, ties away from zero); v - result is exact
+__device__ __forceinline__ float tf32_hi(float v) {
   uint32_t h;
   asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(v));
   return __uint_as_float(h);
 }
 
-// The producers' position in the task's chunk sequence: contribution c, K
-// offset k0 (both advance chunk by chunk).
+// The producers' position in the task's chunk sequence: contribution c (its
+// fields held in registers: every cp.async clobbers memory, so fields read
+// through a pointer would be reloaded before each copy), K offset k0.
 struct TcCursor {
   int c, k0;
+  GemmContrib<float> cb;
 };
+
+__device__ __forceinline__ void tc_cursor_load(TcCursor& u, const GemmContrib<float>* __restrict__ cons, int cend) {
+  while (u.c < cend && cons[u.c].K <= 0) ++u.c;
+  if (u.c < cend) u.cb = cons[u.c];
+}
 
 __device__ __forceinline__ void tc_cursor_next(TcCursor& u, const GemmContrib<float>* __restrict__ cons, int cend) {
   u.k0 += kTcKC;
-  if (u.k0 >= cons[u.c].K) {
+  if (u.k0 >= u.cb.K) {
     u.k0 = 0;
     ++u.c;
-    while (u.c < cend && cons[u.c].K <= 0) ++u.c;
+    tc_cursor_load(u, cons, cend);
   }
 }
 
@@ -312,83 +329,65 @@ __device__ __forceinline__ void tc_cp4(uint32_t dst, const float* src, bool ok) 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
 }
 
-// Producer thread p (0..127) copies its share of one chunk into a raw stage
-// (row r of op(A) at r * kTcRawPitch, row j of op(B)^T after the 128 A rows),
-// coalesced for either storage order: rows contiguous in memory: thread p
-// takes row p, k = 0..15 (a warp reads 32 consecutive rows per k); k
-// contiguous: thread p takes k = p mod 16 of rows p / 16 + 8 j (a warp reads
-// 64 contiguous bytes of two rows).  Positions outside the task (rows >= M /
-// N, k beyond the contribution) are zero-filled.
-__device__ __forceinline__ void tc_copy(const GemmContrib<float>& cb, int k0, int M, int N, int p, uint32_t sraw) {
-  const int kc = min(kTcKC, cb.K - k0);
-  if (!(cb.flags & kTransA)) {   // op(A) = A, M x K column-major: rows contiguous
-    const float* a = cb.A + p + (size_t)k0 * cb.lda;
+// Producer thread q (0..127) of one operand copies its share of a chunk of
+// that operand (R rows, element (r, k) at X[r + k ldx] when rows_contig, else
+// at X[k + r ldx]; K offset k0, kc <= kTcKC values) into its half of a raw
+// stage (row r at r * kTcRawPitch), coalesced either way: rows contiguous:
+// thread q takes row q, k = 0..15 (a warp reads 32 consecutive rows per k);
+// k contiguous: thread q takes k = q mod 16 of rows q / 16 + 8 j (a warp reads
+// 64 contiguous bytes of two rows).  Rows >= R and k >= kc are zero-filled.
+__device__ __forceinline__ void tc_copy(const float* X, int ldx, bool rows_contig, int k0, int kc, int R, int q,
+                                        uint32_t sraw) {
+  if (rows_contig) {
+    const float* x = X + q + (size_t)k0 * ldx;
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      tc_cp4(sraw + 4u * (p * kTcRawPitch + k), p < M && k < kc ? a + (size_t)k * cb.lda : cb.A, p < M && k < kc);
-  } else {                       // op(A) = A^T, A is K x M: k contiguous
-    const int k = p & 15;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int i = (p >> 4) + 8 * j;
-      const bool ok = i < M && k < kc;
-      tc_cp4(sraw + 4u * (i * kTcRawPitch + k), ok ? cb.A + k0 + k + (size_t)i * cb.lda : cb.A, ok);
+    for (int k = 0; k < 16; ++k) {
+      const bool ok = q < R && k < kc;
+      tc_cp4(sraw + 4u * (q * kTcRawPitch + k), ok ? x + (size_t)k * ldx : X, ok);
     }
-  }
-  const uint32_t sb = sraw + 4u * kTileTC * kTcRawPitch;
-  if (cb.flags & kTransB) {      // op(B)^T = B, N x K: rows j contiguous
-    const float* b = cb.B + p + (size_t)k0 * cb.ldb;
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-      tc_cp4(sb + 4u * (p * kTcRawPitch + k), p < N && k < kc ? b + (size_t)k * cb.ldb : cb.B, p < N && k < kc);
-  } else {                       // op(B) = B, K x N column-major: k contiguous
-    const int k = p & 15;
+  } else {
+    const int k = q & 15;
+    const float* x = X + k0 + k + (size_t)(q >> 4) * ldx;
+    const size_t step = (size_t)8 * ldx;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const int i = (p >> 4) + 8 * j;
-      const bool ok = i < N && k < kc;
-      tc_cp4(sb + 4u * (i * kTcRawPitch + k), ok ? cb.B + k0 + k + (size_t)i * cb.ldb : cb.B, ok);
+      const int i = (q >> 4) + 8 * j;
+      const bool ok = i < R && k < kc;
+      tc_cp4(sraw + 4u * (i * kTcRawPitch + k), ok ? x + j * step : X, ok);
     }
   }
 }
 
-// Producer thread p splits row p of op(A) and of op(B)^T from a raw stage
-// into NPART TF32 parts and stores them in the canonical K-major layout
+// Producer thread q splits row q of its operand from a raw stage into NPART
+// parts and stores them in the canonical K-major layout
 template <int NPART>
-__device__ __forceinline__ void tc_split(const float* raw, float* base, int p) {
+__device__ __forceinline__ void tc_split(const float* raw, float* dst, int q) {
+  const float* r = raw + q * kTcRawPitch;
 #pragma unroll
-  for (int mat = 0; mat < 2; ++mat) {
-    const float* r = raw + (mat * kTileTC + p) * kTcRawPitch;
-    float* dst = base + mat * NPART * kTcPartA;
+  for (int kq = 0; kq < kTcKC / 4; ++kq) {
+    const float4 in = *reinterpret_cast<const float4*>(r + 4 * kq);
+    float v[4] = {in.x, in.y, in.z, in.w};
+    const int off = (q >> 3) * (kTcKC / 4) * 32 + kq * 32 + (q & 7) * 4;   // floats
 #pragma unroll
-    for (int kq = 0; kq < kTcKC / 4; ++kq) {
-      const float4 in = *reinterpret_cast<const float4*>(r + 4 * kq);
-      float v[4] = {in.x, in.y, in.z, in.w};
-      const int off = (p >> 3) * (kTcKC / 4) * 32 + kq * 32 + (p & 7) * 4;   // floats
+    for (int part = 0; part < NPART; ++part) {
+      float4 o;
+      float* po = reinterpret_cast<float*>(&o);
 #pragma unroll
-      for (int part = 0; part < NPART; ++part) {
-        float4 o;
-        float* po = reinterpret_cast<float*>(&o);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float h = tf32_rna(v[e]);
-          po[e] = h;
-          v[e] -= h;
-        }
-        *reinterpret_cast<float4*>(dst + part * kTcPartA + off) = o;
+      for (int e = 0; e < 4; ++e) {
+        const float h = tf32_hi(v[e]);
+        po[e] = h;
+        v[e] = __fsub_rn(v[e], h);
       }
+      *reinterpret_cast<float4*>(dst + part * kTcPartA + off) = o;
     }
   }
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
 
@@ -412,7 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   auto acc_full = [&](int b) { return mb + 8u * (2 * kStages + b); };
   auto acc_empty = [&](int b) { return mb + 8u * (2 * kStages + 2 + b); };
   const uint32_t done = mb + 8u * (2 * kStages + 4);
-  if (warp == 4) {
+  if (warp == kTcMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
                  "r"(2 * kTileTC)
@@ -421,12 +420,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   }
   if (tid == 0) {
     for (int st = 0; st < kStages; ++st) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full(st)), "r"(128) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(full(st)), "r"(kTcProd) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(st)) : "memory");
     }
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(acc_full(b)) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(acc_empty(b)), "r"(128) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(acc_empty(b)), "r"(kTcAccWarps * 32) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(done) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -441,19 +440,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   for (int c = tk.c_begin; c < cend; ++c) nch += (max(cons[c].K, 0) + kTcKC - 1) / kTcKC;
   const int ngrp = (nch + kTcFlush - 1) / kTcFlush;
 
-  if (warp < 4) {
+  if (warp < kTcProdWarps) {
     // ---- producers: chunk c is copied into raw stage c mod kTcRaw kTcRaw - 1
     // chunks ahead; once every producer's copies of it have landed (a
-    // producer-only barrier) each thread splits its rows into the operand
-    // stage c mod kStages
-    const int p = tid;
-    const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(raw);
-    TcCursor ld{tk.c_begin, 0};
-    while (ld.c < cend && cons[ld.c].K <= 0) ++ld.c;
+    // producer-only barrier) each thread splits its row into the operand
+    // stage c mod kStages.  Warps 0-3 take op(A), 4-7 op(B)^T.
+    const int mat = warp >> 2, q = tid & (kTileTC - 1);
+    const int R = mat ? N : M;
+    const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(raw) + 4u * mat * kTileTC * kTcRawPitch;
+    TcCursor ld{tk.c_begin, 0, {}};
+    tc_cursor_load(ld, cons, cend);
     int issued = 0;
     auto issue = [&]() {   // one copy group per call (empty past the last chunk)
       if (issued < nch) {
-        tc_copy(cons[ld.c], ld.k0, M, N, p, sraw + 4u * (issued % kTcRaw) * kTcRawStage);
+        const int kc = min(kTcKC, ld.cb.K - ld.k0);
+        const uint32_t dst = sraw + 4u * (issued % kTcRaw) * kTcRawStage;
+        if (mat == 0) tc_copy(ld.cb.A, ld.cb.lda, !(ld.cb.flags & kTransA), ld.k0, kc, R, q, dst);
+        else tc_copy(ld.cb.B, ld.cb.ldb, (ld.cb.flags & kTransB) != 0, ld.k0, kc, R, q, dst);
         tc_cursor_next(ld, cons, cend);
       }
       ++issued;
@@ -463,21 +466,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
     bool bad = false;
     for (int c = 0; c < nch; ++c) {
       asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcRaw - 2) : "memory");
-      asm volatile("bar.sync 1, 128;\n" ::: "memory");   // chunk c landed everywhere; stage c - 1 read
+      asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProd) : "memory");   // chunk c landed everywhere; stage c - 1 read
       issue();                                              // chunk c + kTcRaw - 1 into stage (c - 1) mod kTcRaw
       // a producer whose wait gives up keeps walking the loop (so the
       // producer barrier above never waits for it in vain) without storing
       const int st = c % kStages;
       if (!bad && c >= kStages && !tc_wait(empty(st), (uint32_t)(((c / kStages) + 1) & 1))) bad = true;
       if (!bad) {
-        tc_split<NPART>(raw + (c % kTcRaw) * kTcRawStage, stg + st * Cfg::kStage, p);
+        tc_split<NPART>(raw + (c % kTcRaw) * kTcRawStage + mat * kTileTC * kTcRawPitch,
+                        stg + st * Cfg::kStage + mat * NPART * kTcPartA, q);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full(st)) : "memory");
       }
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (bad) atomicExch(&s_bad, 1);
-  } else if (warp == 4) {
+  } else if (warp == kTcMmaWarp) {
     // ---- MMA issue (one thread)
     if (lane == 0) {
       bool bad = false;
@@ -535,11 +539,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
     __syncwarp();
   } else {
     // ---- accumulators: warp w reads tensor-memory lanes 32 (w mod 4) .. + 31
+    // (the lane quadrant a warp may access), columns col0 .. col0 + 63
     const int qd = warp & 3;
     const int row = 32 * qd + lane;
-    float acc[kTileTC];
+    const int col0 = kTcAccCols * ((warp - kTcAccWarp0) >> 2);
+    float acc[kTcAccCols];
 #pragma unroll
-    for (int j = 0; j < kTileTC; ++j) acc[j] = 0.f;
+    for (int j = 0; j < kTcAccCols; ++j) acc[j] = 0.f;
     bool ok = true;
     for (int g = 0; g < ngrp; ++g) {
       const int b = g & 1;
@@ -547,17 +553,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-      for (int h = 0; h < kTileTC / 64; ++h) {
-        uint32_t r0[32], r1[32];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * kTileTC + 64 * h);
-        tmem_ld32(taddr, r0);
-        tmem_ld32(taddr + 32, r1);
+      for (int h = 0; h < kTcAccCols / 16; ++h) {
+        uint32_t r0[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * kTileTC + col0 + 16 * h), r0);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          acc[64 * h + t] += __uint_as_float(r0[t]);
-          acc[64 * h + 32 + t] += __uint_as_float(r1[t]);
-        }
+        for (int t = 0; t < 16; ++t) acc[16 * h + t] += __uint_as_float(r0[t]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(acc_empty(b)) : "memory");
@@ -566,26 +567,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();   // (1) every role has finished its loop and recorded failures
     const bool poisoned = s_bad != 0;
-    if (row < M) {
+    // the task is read again here rather than kept live through the loop
+    const GemmTask<float> te = tasks[blockIdx.x];
+    if (row < te.M) {
+      float* pc = te.C + (size_t)row + (size_t)col0 * te.ldc;
 #pragma unroll
-      for (int j = 0; j < kTileTC; ++j) {
-        if (j < N) {
-          float* pc = tk.C + (size_t)row + (size_t)j * tk.ldc;
+      for (int jj = 0; jj < kTcAccCols; ++jj) {
+        if (col0 + jj < te.N) {
           if (nch == 0) {
-            if (!tk.beta) *pc = 0.f;
+            if (!te.beta) *pc = 0.f;
           } else {
-            float v = poisoned ? __int_as_float(0x7fc00000) : tk.alpha * acc[j];
-            if (tk.beta) v += *pc;
+            float v = poisoned ? __int_as_float(0x7fc00000) : te.alpha * acc[jj];
+            if (te.beta) v += *pc;
             *pc = v;
           }
         }
+        pc += te.ldc;
       }
     }
     return;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();   // (1)
-  if (warp == 4) {
+  if (warp == kTcMmaWarp) {
     // the tensor memory is released only once every product issued has
     // completed (the commit tracks them all), or the bounded wait gave up
     tc_wait(done, 0u);

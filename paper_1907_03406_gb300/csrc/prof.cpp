@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
+#include <string>
 #include <vector>
 
 namespace sgf {
@@ -17,6 +18,7 @@ struct Pending {
   cudaEvent_t a, b;
   int kind;
   double flops, bytes;
+  std::string note;
 };
 struct State {
   std::mutex mu;
@@ -24,6 +26,7 @@ struct State {
   int timing = 0;
   double next_flops = 0, next_bytes = 0;
   double next_flops_seen = 0, next_bytes_seen = 0;   // work of the launch being opened
+  std::string next_note;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
 };
@@ -51,14 +54,22 @@ void drain(State& S) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) S.acc[p.kind].ms += ms;
     if (g_log)
-      std::fprintf(stderr, "[sgf launch] %-10s flops %.4e bytes %.4e ms %.5f GB/s %.1f\n", prof_name(p.kind),
-                   p.flops, p.bytes, ms, ms > 0 ? p.bytes / (ms * 1e-3) / 1e9 : 0.0);
+      std::fprintf(stderr, "[sgf launch] %-10s flops %.4e bytes %.4e ms %.5f GB/s %.1f %s\n", prof_name(p.kind),
+                   p.flops, p.bytes, ms, ms > 0 ? p.bytes / (ms * 1e-3) / 1e9 : 0.0, p.note.c_str());
     S.pool.push_back(p.a);
     S.pool.push_back(p.b);
   }
   S.pending.clear();
 }
 }  // namespace
+
+bool prof_logging() { return g_log; }
+
+void prof_note(const char* note) {
+  State& S = st();
+  std::lock_guard<std::mutex> g(S.mu);
+  S.next_note = note ? note : "";
+}
 
 void prof_work(double flops, double bytes) {
   State& S = st();
@@ -70,6 +81,8 @@ void prof_work(double flops, double bytes) {
 ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
   State& S = st();
   std::lock_guard<std::mutex> g(S.mu);
+  std::string note;
+  note.swap(S.next_note);
   if (t_capturing) {
     S.next_flops = S.next_bytes = 0;
     return;
@@ -89,6 +102,7 @@ ProfScope::ProfScope(int kind, cudaStream_t s) : kind_(kind), s_(s), slot_(-1) {
     p.kind = kind;
     p.flops = S.next_flops_seen;
     p.bytes = S.next_bytes_seen;
+    p.note = std::move(note);
     cudaEventRecord(p.a, s);
     S.pending.push_back(p);
     slot_ = (int)S.pending.size() - 1;

@@ -17,6 +17,11 @@ enum ProfKind {
 
 // work of the next launch (set by the code that built its tasks)
 void prof_work(double flops, double bytes);
+// a description of the next launch, printed beside it in the launch log
+// (SGF_PROF_LOG); copied
+void prof_note(const char* note);
+// whether the launch log is on
+bool prof_logging();
 
 class ProfScope {
  public:
