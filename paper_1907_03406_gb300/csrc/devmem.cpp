@@ -59,11 +59,16 @@ static std::atomic<int64_t> g_alloc_events{0};
 void note_alloc_event() { g_alloc_events.fetch_add(1, std::memory_order_relaxed); }
 int64_t alloc_events() { return g_alloc_events.load(std::memory_order_relaxed); }
 
+static void check_aligned(void* p) {
+  if (reinterpret_cast<uintptr_t>(p) & 15) throw SgfError(SGF_ERR_CUDA, "device allocation not 16-byte aligned");
+}
+
 void* dev_malloc(size_t bytes) {
   if (dry_run()) return fake_alloc(bytes);
   void* p = nullptr;
   note_alloc_event();
-  SGF_CK(cudaMalloc(&p, bytes));
+  SGF_CK(cudaMalloc(&p, bytes + kAllocTail));
+  check_aligned(p);
   return p;
 }
 void dev_free(void* p) {
@@ -92,16 +97,17 @@ void* dev_malloc_async(size_t bytes, cudaStream_t s) {
   }
   void* p = nullptr;
   note_alloc_event();
-  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  cudaError_t e = cudaMallocAsync(&p, bytes + kAllocTail, s);
   if (e == cudaErrorMemoryAllocation) {
     // the pool may be holding freed blocks of earlier factorizations: hand
     // them back to the device and try once more
     cudaGetLastError();
     cudaStreamSynchronize(s);
     dev_release_cached();
-    e = cudaMallocAsync(&p, bytes, s);
+    e = cudaMallocAsync(&p, bytes + kAllocTail, s);
   }
   SGF_CK(e);
+  check_aligned(p);
   return p;
 }
 void dev_release_cached() {
@@ -159,6 +165,27 @@ void check_range(const void* p, size_t bytes, const char* what) {
   }
   if (!ok) {
     if (r.violations < 20) r.log << what << ": [" << std::hex << a << ", +" << std::dec << bytes << ") outside any allocation\n";
+    r.violations++;
+  }
+}
+
+void check_block_superset(const void* p, int64_t M, int64_t N, int64_t ld, size_t es, const char* what) {
+  if (!dry_run() || M <= 0 || N <= 0 || g_skip_checks) return;
+  const uintptr_t a = (uintptr_t)p;
+  const uintptr_t a0 = a & ~uintptr_t(15);
+  const uintptr_t e1 = (a + (size_t)((M - 1) + (N - 1) * ld + 1) * es + 15) & ~uintptr_t(15);
+  Registry& r = reg();
+  std::lock_guard<std::mutex> g(r.mu);
+  r.checks++;
+  auto it = r.live.upper_bound(a0);
+  bool ok = false;
+  if (it != r.live.begin()) {
+    --it;
+    ok = a0 >= it->first && e1 <= it->first + it->second + kAllocTail;
+  }
+  if (!ok) {
+    if (r.violations < 20)
+      r.log << what << ": aligned superset [" << std::hex << a0 << ", " << e1 << std::dec << ") outside any allocation and its tail\n";
     r.violations++;
   }
 }

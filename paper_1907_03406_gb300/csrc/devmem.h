@@ -17,6 +17,11 @@ namespace sgf {
 
 bool dry_run();
 
+// Every device allocation is 16-byte aligned and kAllocTail bytes longer than
+// asked for, so a kernel may read the 16-byte aligned superset of any segment
+// it owns (bulk copies need aligned ends) without leaving the allocation.
+constexpr size_t kAllocTail = 64;
+
 void* dev_malloc(size_t bytes);                          // persistent (cudaMalloc)
 void dev_free(void* p);
 // stream ordered, from the device's default pool, which keeps freed blocks
@@ -41,6 +46,9 @@ void dev_sync(cudaStream_t s);
 void check_range(const void* p, size_t bytes, const char* what);
 // column-major M x N block with leading dimension ld and element size es
 void check_block(const void* p, int64_t M, int64_t N, int64_t ld, size_t es, const char* what);
+// the 16-byte aligned superset of that block's columns (what bulk copies of
+// its column segments read) lies in one live allocation and its tail
+void check_block_superset(const void* p, int64_t M, int64_t N, int64_t ld, size_t es, const char* what);
 int64_t dry_run_violations();
 void dry_run_reset();
 std::string dry_run_report();

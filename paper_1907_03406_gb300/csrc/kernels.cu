@@ -218,19 +218,22 @@ __global__ void __launch_bounds__(kThreads) k_gemm<float>(const GemmTask<float>*
 // tensor-core tile GEMM (FP32 operands as split TF32 products, FP32 accumulation)
 // ---------------------------------------------------------------------------
 // One CTA per kTileTC x kTileTC output tile (M, N <= 128); the contributions'
-// K ranges are walked in chunks of kTcKC.  Seventeen warps, specialized, with
-// no CTA barrier in the main loop:
+// K ranges are walked in raw chunks of kRawK values and, within them, in
+// chunks of kTcKC.  Seventeen warps, specialized, with no CTA barrier in the
+// main loop:
 //  * warps 0-7 (producers: warps 0-3 for op(A), 4-7 for op(B)^T, thread q of
-//    a group owning row q of its operand) copy chunk c + 3 from global memory
-//    into a raw shared-memory ring by 4-byte cp.async (coalesced whichever
-//    index of an operand is contiguous), then, once chunk c has landed for
-//    all of them (a barrier among the producers only), split their rows of it
+//    a group owning row q of its operand) bring each raw chunk of both
+//    operands one chunk ahead into one of two raw shared-memory stages with
+//    cp.async.bulk (a copy per row of a K-contiguous operand, per k-row of a
+//    row-contiguous one; the node blocks have odd leading dimensions, so each
+//    copy takes the 16-byte aligned superset of its segment), then split
+//    their row of each raw chunk
 //    into NPART TF32 parts (each the remainder so far rounded to nearest
-//    TF32, so v = p0 + p1 [+ p2] up to the last part's rounding) and store
-//    them K-major in the no-swizzle canonical layout
-//    (core matrices of 8 rows x 16 bytes, 128 bytes apart along K, kTcKC / 4
-//    * 128 bytes apart along rows) into operand stage c mod kStages, then
-//    arrive on the stage's "full" mbarrier;
+//    TF32, so v = p0 + p1 [+ p2] up to the last part's rounding), store them
+//    K-major in the no-swizzle canonical layout (core matrices of 8 rows x 16
+//    bytes, 128 bytes apart along K, kTcKC / 4 * 128 bytes apart along rows)
+//    into operand stage c mod kStages and arrive on its "full" mbarrier; a
+//    producer-only barrier after each raw chunk frees its raw stage;
 //  * one thread of warp 8 waits for "full", issues per 8-wide K step the
 //    split products (NPART = 2: p0q0 + p0q1 + p1q0, the 3xTF32 scheme;
 //    NPART = 3: also p0q2 + p1q1 + p2q0) as tcgen05.mma kind::tf32 (M = N =
@@ -258,16 +261,22 @@ constexpr int kTcAccWarps = 8;
 constexpr int kTcAccCols = kTileTC * 4 / kTcAccWarps;   // columns per accumulator warp
 constexpr int kTcThreads = (kTcAccWarp0 + kTcAccWarps) * 32;
 constexpr int kTcPartA = kTileTC * kTcKC;    // floats of one operand part per stage
-constexpr int kTcRawPitch = 20;              // raw chunk rows: 16 values + pad (16-byte aligned, few conflicts)
-constexpr int kTcRawStage = 2 * kTileTC * kTcRawPitch;   // floats: op(A) rows then op(B)^T rows
-constexpr int kTcRaw = 4;                    // raw ring depth: kTcRaw - 1 chunks in flight
+constexpr int kTcPitchR = 136;               // raw k-row of a row-contiguous operand: 128 values + alignment slack
 constexpr int kTcWaitIters = 1 << 22;
 
+// Shared memory: kStages split-operand stages, then two raw stages (each
+// op(A) then op(B)^T, kRawOp floats apiece) of kRawK values of K.  A raw
+// row (K-contiguous operand, pitch kPitchK) holds the aligned superset of
+// kRawK values; the pitch is 12 mod 32 words, so eight consecutive rows'
+// 16-byte reads meet eight different bank groups.
 template <int NPART>
 struct TcCfg {
-  static constexpr int kStages = NPART == 2 ? 4 : 2;    // split operand stages
+  static constexpr int kStages = 2;
   static constexpr int kStage = 2 * NPART * kTcPartA;   // A and B parts
-  static constexpr size_t kSmem = sizeof(float) * ((size_t)kStages * kStage + (size_t)kTcRaw * kTcRawStage);
+  static constexpr int kRawK = NPART == 2 ? 64 : 32;
+  static constexpr int kPitchK = NPART == 2 ? 76 : 44;
+  static constexpr int kRawOp = kTileTC * kPitchK > kRawK * kTcPitchR ? kTileTC * kPitchK : kRawK * kTcPitchR;
+  static constexpr size_t kSmem = sizeof(float) * ((size_t)kStages * kStage + 4 * (size_t)kRawOp);
 };
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
@@ -315,8 +324,9 @@ __device__ __forceinline__ void tc_cursor_load(TcCursor& u, const GemmContrib<fl
   if (u.c < cend) u.cb = cons[u.c];
 }
 
-__device__ __forceinline__ void tc_cursor_next(TcCursor& u, const GemmContrib<float>* __restrict__ cons, int cend) {
-  u.k0 += kTcKC;
+__device__ __forceinline__ void tc_cursor_next(TcCursor& u, const GemmContrib<float>* __restrict__ cons, int cend,
+                                               int step) {
+  u.k0 += step;
   if (u.k0 >= u.cb.K) {
     u.k0 = 0;
     ++u.c;
@@ -324,49 +334,88 @@ __device__ __forceinline__ void tc_cursor_next(TcCursor& u, const GemmContrib<fl
   }
 }
 
-__device__ __forceinline__ void tc_cp4(uint32_t dst, const float* src, bool ok) {
-  // 4-byte asynchronous copy; zero-filled (nothing read) when !ok
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
-}
-
-// Producer thread q (0..127) of one operand copies its share of a chunk of
-// that operand (R rows, element (r, k) at X[r + k ldx] when rows_contig, else
-// at X[k + r ldx]; K offset k0, kc <= kTcKC values) into its half of a raw
-// stage (row r at r * kTcRawPitch), coalesced either way: rows contiguous:
-// thread q takes row q, k = 0..15 (a warp reads 32 consecutive rows per k);
-// k contiguous: thread q takes k = q mod 16 of rows q / 16 + 8 j (a warp reads
-// 64 contiguous bytes of two rows).  Rows >= R and k >= kc are zero-filled.
-__device__ __forceinline__ void tc_copy(const float* X, int ldx, bool rows_contig, int k0, int kc, int R, int q,
-                                        uint32_t sraw) {
+// Producer thread q (0..127) of one operand issues its bulk copy of a raw
+// chunk of that operand (R rows, element (r, k) at X[r + k ldx] when
+// rows_contig, else at X[k + r ldx]; K offset k0, kc <= kRawK values) into
+// the operand's half of a raw stage, and arrives on the stage's mbarrier
+// with the bytes it expects (every producer thread arrives, with 0 bytes
+// when it has nothing to copy).  K contiguous: thread q copies row q's kc
+// values; rows contiguous: thread q (< kc) copies k-row q's R values and
+// records where that k-row starts in its superset in the shift table.  A
+// bulk copy needs 16-byte aligned ends, so each takes the aligned superset
+// of its segment: at most 12 bytes either side, inside the allocation and
+// its tail (every device allocation keeps one).
+template <int NPART>
+__device__ __forceinline__ void tc_issue(const float* X, int ldx, bool rows_contig, int k0, int kc, int R, int q,
+                                         uint32_t sraw, uint32_t bar, unsigned char* shtab) {
+  using Cfg = TcCfg<NPART>;
+  uintptr_t a = 0;
+  uint32_t dst = 0, nb = 0;
   if (rows_contig) {
-    const float* x = X + q + (size_t)k0 * ldx;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const bool ok = q < R && k < kc;
-      tc_cp4(sraw + 4u * (q * kTcRawPitch + k), ok ? x + (size_t)k * ldx : X, ok);
+    if (q < kc && R > 0) {
+      a = reinterpret_cast<uintptr_t>(X + (size_t)(k0 + q) * ldx);
+      nb = (uint32_t)(((a + sizeof(float) * R + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)));
+      dst = sraw + 4u * q * kTcPitchR;
+      shtab[q] = (unsigned char)((a & 15) >> 2);   // published by the arrival below
     }
   } else {
-    const int k = q & 15;
-    const float* x = X + k0 + k + (size_t)(q >> 4) * ldx;
-    const size_t step = (size_t)8 * ldx;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int i = (q >> 4) + 8 * j;
-      const bool ok = i < R && k < kc;
-      tc_cp4(sraw + 4u * (i * kTcRawPitch + k), ok ? x + j * step : X, ok);
+    if (q < R && kc > 0) {
+      a = reinterpret_cast<uintptr_t>(X + (size_t)q * ldx + k0);
+      nb = (uint32_t)(((a + sizeof(float) * kc + 15) & ~uintptr_t(15)) - (a & ~uintptr_t(15)));
+      dst = sraw + 4u * q * Cfg::kPitchK;
     }
+  }
+  if (nb) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(nb) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     dst),
+                 "l"(a & ~uintptr_t(15)), "r"(nb), "r"(bar)
+                 : "memory");
+  } else {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
   }
 }
 
-// Producer thread q splits row q of its operand from a raw stage into NPART
-// parts and stores them in the canonical K-major layout
+// Producer thread q takes row q of its operand, values kk0 .. kk0 + 15 of
+// the raw chunk (zero for rows >= R and k >= kc), splits them into NPART
+// parts and stores them in the canonical K-major layout.  Where a segment
+// starts in its superset: K contiguous, the row's own address (one shift
+// for all its values, applied by branch-free selects on 16-byte reads);
+// rows contiguous, the shift table the issuing threads wrote.
 template <int NPART>
-__device__ __forceinline__ void tc_split(const float* raw, float* dst, int q) {
-  const float* r = raw + q * kTcRawPitch;
+__device__ __forceinline__ void tc_split(const float* raw, const unsigned char* shtab, const float* X, int ldx,
+                                         bool rows_contig, int k0, int kk0, int kc, int R, int q, float* dst) {
+  using Cfg = TcCfg<NPART>;
+  float v[16];
+  if (rows_contig) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int kk = kk0 + j;
+      v[j] = (q < R && kk < kc) ? raw[kk * kTcPitchR + shtab[kk] + q] : 0.f;
+    }
+  } else {
+    const int sh = (int)((reinterpret_cast<uintptr_t>(X + (size_t)q * ldx + k0) & 15) >> 2);
+    float a[20];
+    const float* rp = raw + q * Cfg::kPitchK + kk0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const float4 f = *reinterpret_cast<const float4*>(rp + 4 * m);
+      a[4 * m] = f.x;
+      a[4 * m + 1] = f.y;
+      a[4 * m + 2] = f.z;
+      a[4 * m + 3] = f.w;
+    }
+    const bool s1 = sh & 1, s2 = sh & 2, live = q < R;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float w0 = s1 ? a[j + 1] : a[j];
+      const float w1 = s1 ? a[j + 3] : a[j + 2];
+      const float w = s2 ? w1 : w0;
+      v[j] = (live && kk0 + j < kc) ? w : 0.f;
+    }
+  }
 #pragma unroll
   for (int kq = 0; kq < kTcKC / 4; ++kq) {
-    const float4 in = *reinterpret_cast<const float4*>(r + 4 * kq);
-    float v[4] = {in.x, in.y, in.z, in.w};
     const int off = (q >> 3) * (kTcKC / 4) * 32 + kq * 32 + (q & 7) * 4;   // floats
 #pragma unroll
     for (int part = 0; part < NPART; ++part) {
@@ -374,9 +423,9 @@ __device__ __forceinline__ void tc_split(const float* raw, float* dst, int q) {
       float* po = reinterpret_cast<float*>(&o);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float h = tf32_hi(v[e]);
+        const float h = tf32_hi(v[4 * kq + e]);
         po[e] = h;
-        v[e] = __fsub_rn(v[e], h);
+        v[4 * kq + e] = __fsub_rn(v[4 * kq + e], h);
       }
       *reinterpret_cast<float4*>(dst + part * kTcPartA + off) = o;
     }
@@ -399,11 +448,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   const GemmTask<float> tk = tasks[blockIdx.x];
   extern __shared__ __align__(1024) unsigned char tc_smraw[];
   float* stg = reinterpret_cast<float*>(tc_smraw);   // kStages x [A parts | B parts]
-  float* raw = stg + kStages * Cfg::kStage;           // kTcRaw x [A rows | B rows]
-  // full[s], empty[s], acc_full[2], acc_empty[2], done
-  __shared__ __align__(8) uint64_t mbar[2 * kStages + 5];
+  float* raw = stg + kStages * Cfg::kStage;           // 2 x [A | B] raw chunks
+  // full[s], empty[s], acc_full[2], acc_empty[2], done, raw_full[2]
+  __shared__ __align__(8) uint64_t mbar[2 * kStages + 7];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_bad;
+  __shared__ unsigned char shtab[2][2][64];   // [raw stage][operand][k-row]: start of a row-contiguous k-row
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
   auto full = [&](int st) { return mb + 8u * st; };
@@ -411,6 +461,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   auto acc_full = [&](int b) { return mb + 8u * (2 * kStages + b); };
   auto acc_empty = [&](int b) { return mb + 8u * (2 * kStages + 2 + b); };
   const uint32_t done = mb + 8u * (2 * kStages + 4);
+  auto raw_full = [&](int rs) { return mb + 8u * (2 * kStages + 5 + rs); };
   if (warp == kTcMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
@@ -428,6 +479,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(acc_empty(b)), "r"(kTcAccWarps * 32) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(done) : "memory");
+    for (int rs = 0; rs < 2; ++rs)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(raw_full(rs)), "r"(kTcProd) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     s_bad = 0;
   }
@@ -441,45 +494,55 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gemm_tc(const GemmTask<float>
   const int ngrp = (nch + kTcFlush - 1) / kTcFlush;
 
   if (warp < kTcProdWarps) {
-    // ---- producers: chunk c is copied into raw stage c mod kTcRaw kTcRaw - 1
-    // chunks ahead; once every producer's copies of it have landed (a
-    // producer-only barrier) each thread splits its row into the operand
-    // stage c mod kStages.  Warps 0-3 take op(A), 4-7 op(B)^T.
+    // ---- producers: raw chunk rc (kRawK values of K of one contribution) is
+    // bulk-copied into raw stage rc mod 2 one chunk ahead; once it has landed
+    // (its mbarrier) each thread splits its row of it, 16 values at a time,
+    // into the operand stages (c mod kStages for the task's c-th 16-value
+    // chunk).  Warps 0-3 take op(A), 4-7 op(B)^T.  A producer-only barrier
+    // after each raw chunk frees its stage for the copies two chunks on.  A
+    // producer whose wait gives up keeps walking the loop (arriving and
+    // meeting the barrier, so no other producer waits for it in vain)
+    // without storing.
     const int mat = warp >> 2, q = tid & (kTileTC - 1);
     const int R = mat ? N : M;
-    const uint32_t sraw = (uint32_t)__cvta_generic_to_shared(raw) + 4u * mat * kTileTC * kTcRawPitch;
-    TcCursor ld{tk.c_begin, 0, {}};
-    tc_cursor_load(ld, cons, cend);
-    int issued = 0;
-    auto issue = [&]() {   // one copy group per call (empty past the last chunk)
-      if (issued < nch) {
-        const int kc = min(kTcKC, ld.cb.K - ld.k0);
-        const uint32_t dst = sraw + 4u * (issued % kTcRaw) * kTcRawStage;
-        if (mat == 0) tc_copy(ld.cb.A, ld.cb.lda, !(ld.cb.flags & kTransA), ld.k0, kc, R, q, dst);
-        else tc_copy(ld.cb.B, ld.cb.ldb, (ld.cb.flags & kTransB) != 0, ld.k0, kc, R, q, dst);
-        tc_cursor_next(ld, cons, cend);
-      }
-      ++issued;
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const uint32_t raw0 = (uint32_t)__cvta_generic_to_shared(raw);
+    TcCursor is{tk.c_begin, 0, {}};   // next raw chunk to copy
+    tc_cursor_load(is, cons, cend);
+    TcCursor sp = is;                 // raw chunk being split
+    auto issue = [&](int rc) {
+      const int rs = rc & 1, kc = min(Cfg::kRawK, is.cb.K - is.k0);
+      const uint32_t dst = raw0 + 4u * (uint32_t)((2 * rs + mat) * Cfg::kRawOp);
+      if (mat == 0)
+        tc_issue<NPART>(is.cb.A, is.cb.lda, !(is.cb.flags & kTransA), is.k0, kc, R, q, dst, raw_full(rs), shtab[rs][0]);
+      else
+        tc_issue<NPART>(is.cb.B, is.cb.ldb, (is.cb.flags & kTransB) != 0, is.k0, kc, R, q, dst, raw_full(rs), shtab[rs][1]);
+      tc_cursor_next(is, cons, cend, Cfg::kRawK);
     };
-    for (int k = 0; k < kTcRaw - 1; ++k) issue();
     bool bad = false;
-    for (int c = 0; c < nch; ++c) {
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcRaw - 2) : "memory");
-      asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProd) : "memory");   // chunk c landed everywhere; stage c - 1 read
-      issue();                                              // chunk c + kTcRaw - 1 into stage (c - 1) mod kTcRaw
-      // a producer whose wait gives up keeps walking the loop (so the
-      // producer barrier above never waits for it in vain) without storing
-      const int st = c % kStages;
-      if (!bad && c >= kStages && !tc_wait(empty(st), (uint32_t)(((c / kStages) + 1) & 1))) bad = true;
-      if (!bad) {
-        tc_split<NPART>(raw + (c % kTcRaw) * kTcRawStage + mat * kTileTC * kTcRawPitch,
-                        stg + st * Cfg::kStage + mat * NPART * kTcPartA, q);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full(st)) : "memory");
+    int c = 0;
+    if (is.c < cend) issue(0);
+    for (int rc = 0; sp.c < cend; ++rc) {
+      if (is.c < cend) issue(rc + 1);
+      if (!bad && !tc_wait(raw_full(rc & 1), (uint32_t)((rc >> 1) & 1))) bad = true;
+      const float* rawop = raw + (2 * (rc & 1) + mat) * Cfg::kRawOp;
+      const unsigned char* sht = shtab[rc & 1][mat];
+      const int kc = min(Cfg::kRawK, sp.cb.K - sp.k0);
+      for (int kk0 = 0; kk0 < kc; kk0 += kTcKC, ++c) {
+        const int st = c % kStages;
+        if (!bad && c >= kStages && !tc_wait(empty(st), (uint32_t)(((c / kStages) + 1) & 1))) bad = true;
+        if (!bad) {
+          float* dst = stg + st * Cfg::kStage + mat * NPART * kTcPartA;
+          if (mat == 0)
+            tc_split<NPART>(rawop, sht, sp.cb.A, sp.cb.lda, !(sp.cb.flags & kTransA), sp.k0, kk0, kc, R, q, dst);
+          else
+            tc_split<NPART>(rawop, sht, sp.cb.B, sp.cb.ldb, (sp.cb.flags & kTransB) != 0, sp.k0, kk0, kc, R, q, dst);
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full(st)) : "memory");
+        }
       }
+      tc_cursor_next(sp, cons, cend, Cfg::kRawK);
+      asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProd) : "memory");   // raw stage rc mod 2 read by every producer
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (bad) atomicExch(&s_bad, 1);
   } else if (warp == kTcMmaWarp) {
     // ---- MMA issue (one thread)
@@ -1828,10 +1891,11 @@ void launch_gemm_tc(const GemmTask<float>* tasks, const GemmContrib<float>* cons
       check_block(t.C, t.M, t.N, t.ldc, sizeof(float), "tc gemm C");
       for (int c = t.c_begin; c < t.c_begin + t.c_count; ++c) {
         const GemmContrib<float>& q = cons[c];
-        if (q.flags & kTransA) check_block(q.A, q.K, t.M, q.lda, sizeof(float), "tc gemm A^T");
-        else check_block(q.A, t.M, q.K, q.lda, sizeof(float), "tc gemm A");
-        if (q.flags & kTransB) check_block(q.B, t.N, q.K, q.ldb, sizeof(float), "tc gemm B^T");
-        else check_block(q.B, q.K, t.N, q.ldb, sizeof(float), "tc gemm B");
+        // (the bulk copies read the 16-byte aligned supersets of the segments)
+        if (q.flags & kTransA) check_block_superset(q.A, q.K, t.M, q.lda, sizeof(float), "tc gemm A^T");
+        else check_block_superset(q.A, t.M, q.K, q.lda, sizeof(float), "tc gemm A");
+        if (q.flags & kTransB) check_block_superset(q.B, t.N, q.K, q.ldb, sizeof(float), "tc gemm B^T");
+        else check_block_superset(q.B, q.K, t.N, q.ldb, sizeof(float), "tc gemm B");
       }
     }
     return;
