@@ -325,6 +325,15 @@ struct GemmList {
       add(C + i0, ldc, std::min(tm, M - i0), N, T(1), 0, {{Li + i0, ldli, false, B, ldb, false, K}});
     }
   }
+  // C[M x N] = Li^T B with Li lower triangular (M x M): the row band starting
+  // at i0 needs only rows i0.. of B (column i0 + r of Li is zero above row
+  // i0 + r)
+  void add_lowtri_t(T* C, int ldc, int M, int N, const T* Li, int ldli, const T* B, int ldb) {
+    const int tm = use_tc(M, N) ? kTileTC : kTile;
+    for (int i0 = 0; i0 < M; i0 += tm)
+      add(C + i0, ldc, std::min(tm, M - i0), N, T(1), 0,
+          {{Li + i0 + (size_t)i0 * ldli, ldli, true, B + i0, ldb, false, M - i0}});
+  }
   static void work(const std::vector<GemmTask<T>>& v, const std::vector<GemmContrib<T>>& c, double& fl, double& by) {
     fl = by = 0;
     for (const auto& g : v) {
@@ -532,8 +541,10 @@ T* walloc(std::vector<void*>& work, size_t count, cudaStream_t s, bool zero = tr
 template <typename T>
 struct InteriorRec {
   int node, m, s;
-  T *L, *Li, *W;
-  T* Wt;   // W^T (s x m), for the apply's backward W x_S as column dot products
+  T *L, *Li, *W;   // Li: only while the level is factored
+  // for the apply: Z = L^{-T} W = A_II^{-1} A_IS (m x s) and its transpose
+  // Zt (s x m), and Ai = L^{-T} L^{-1} = A_II^{-1} (m x m), all column-major
+  T *Z, *Zt, *Ai;
   std::vector<std::pair<int, int>> nb;  // (separator, column offset in W)
 };
 
@@ -1137,7 +1148,7 @@ class FactorImpl final : public FactorBase {
         r.L = Dg + lay.dg_off[i];
         r.Li = LiI + li_off[i];
         r.W = Wb + w_off[i];
-        r.Wt = nullptr;
+        r.Z = r.Zt = r.Ai = nullptr;
         for (int k = lay.up_ptr[i]; k < lay.up_ptr[i + 1]; ++k) r.nb.push_back({lay.up_nb[k], lay.up_col[k]});
         rec.in.push_back(r);
       }
@@ -1543,27 +1554,50 @@ class FactorImpl final : public FactorBase {
         }
         rec.sep.push_back(sr);
       }
-      // apply layout: mirrored inverse factors and W^T (the factor is done with
-      // the zero upper triangles of L^{-1} at this point)
+      // apply layout (the factor is done with the zero upper triangles of the
+      // L^{-1} blocks at this point).  Interiors: the apply uses, instead of
+      // L^{-1} and W, Z = L^{-T} W = A_II^{-1} A_IS, its transpose and
+      // A_II^{-1} = L^{-T} L^{-1} (the same bytes in all, but only dense
+      // blocks); L^{-1} is freed.  Compressed separators: L_B^{-1} mirrored.
       {
-        int64_t wt_tot = 0;
-        for (const auto& r : rec.in) wt_tot += (int64_t)r.m * r.s;
-        T* Wt = dalloc<T>(keep_, wt_tot, s, false);
-        CopyList<T, T> cm;
-        int64_t off = 0;
-        for (auto& r : rec.in) {
-          add_mirror(cm, r.Li, r.m);
-          r.Wt = Wt + off;
-          off += (int64_t)r.m * r.s;
-          if (r.s > 0) cm.add(r.W, r.m, r.Wt, r.s, r.s, r.m, kCopyT);
+        int64_t zs = 0, as = 0;
+        for (const auto& r : rec.in) {
+          zs += (int64_t)r.m * r.s;
+          as += (int64_t)r.m * r.m;
         }
+        T* Zb = dalloc<T>(keep_, zs, s, false);
+        T* Ztb = dalloc<T>(keep_, zs, s, false);
+        T* Ab = dalloc<T>(keep_, as, s, false);
+        GemmList<T> gz;
+        int64_t oz = 0, oa = 0;
+        for (auto& r : rec.in) {
+          r.Z = Zb + oz;
+          r.Zt = Ztb + oz;
+          r.Ai = Ab + oa;
+          oz += (int64_t)r.m * r.s;
+          oa += (int64_t)r.m * r.m;
+          if (r.s > 0) gz.add_lowtri_t(r.Z, r.m, r.m, r.s, r.Li, r.m, r.W, r.m);
+          gz.add_lowtri_t(r.Ai, r.m, r.m, r.m, r.Li, r.m, r.Li, r.m);
+        }
+        gz.emit(b, s);
+        b.run(s);
+        CopyList<T, T> cm;
+        for (auto& r : rec.in)
+          if (r.s > 0) cm.add(r.Z, r.m, r.Zt, r.s, r.s, r.m, kCopyT);
         for (const auto& sr : rec.sep)
           if (sr.comp) add_mirror(cm, sr.Li, sr.m);
         cm.emit(b, s);
         b.run(s);
+        // the interiors' L^{-1} blocks are not read again
+        auto it = std::find(keep_.begin(), keep_.end(), (void*)LiI);
+        if (it != keep_.end()) {
+          keep_.erase(it);
+          dev_free_async(LiI, s);
+        }
+        for (auto& r : rec.in) r.Li = nullptr;
       }
       int64_t bytes = 0;
-      for (const auto& r : rec.in) bytes += ((int64_t)2 * r.m * r.m + (int64_t)2 * r.m * r.s) * sizeof(T);
+      for (const auto& r : rec.in) bytes += ((int64_t)2 * r.m * r.m + (int64_t)3 * r.m * r.s) * sizeof(T);
       for (const auto& r : rec.sep)
         if (r.comp) bytes += ((int64_t)2 * r.m * r.m + (int64_t)r.m * r.k) * sizeof(T);
       ls.bytes = bytes;
@@ -1690,24 +1724,22 @@ class FactorImpl final : public FactorBase {
     T* v = base(t);
     T* w = v + vs * nr;
     T* kp = v + 2 * vs * nr;
-    // every large product is a column dot product: L^{-1} x through the
-    // mirrored upper triangle, W^T x and L^{-T} x through the columns
-    GemvList<T> f1(nr), f2(nr), f3(nr), f4(nr);
-    f1.trans = f2.trans = f3.trans = f4.trans = true;
-    f1.tag = "L" + std::to_string(t) + ".f1";
+    // every large product is a column dot product: Z^T x through the
+    // columns of Z (v_S -= A_SI A_II^{-1} v_I = W^T L^{-1} v_I), then for the
+    // compressed separators L_B^{-1} x through the mirrored upper triangle
+    // and Q1^T x
+    GemvList<T> f2(nr), f3(nr), f4(nr);
+    f2.trans = f3.trans = f4.trans = true;
     f2.tag = "L" + std::to_string(t) + ".f2";
     f3.tag = "L" + std::to_string(t) + ".f3";
     f4.tag = "L" + std::to_string(t) + ".f4";
-    for (const auto& r : R.in)
-      f1.add(w + nr * lay.vec_off[r.node], r.m, 0,
-             {{r.Li, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1), true}});
     auto si = sep_interiors(R, (int)lay.m.size());
     for (int S = 0; S < (int)si.size(); ++S) {
       if (si[S].empty()) continue;
       std::vector<typename GemvList<T>::In> ins;
       for (auto [a, col] : si[S]) {
         const auto& r = R.in[a];
-        ins.push_back({r.W + (size_t)col * r.m, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
+        ins.push_back({r.Z + (size_t)col * r.m, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
       }
       f2.add(v + nr * lay.vec_off[S], lay.m[S], 1, ins);
     }
@@ -1717,7 +1749,6 @@ class FactorImpl final : public FactorBase {
              {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1), true}});
       f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
     }
-    f1.emit(P, s);
     f2.emit(P, s);
     f3.emit(P, s);
     f4.emit(P, s);
@@ -1754,20 +1785,21 @@ class FactorImpl final : public FactorBase {
     for (const auto& c : R.sep)
       if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
     veccopy(P, vc, vn, v);
-    GemvList<T> b1(nr), b2(nr), b3(nr), b4(nr);
-    b2.trans = b3.trans = b4.trans = true;
+    GemvList<T> b1(nr), b2(nr), b3(nr);
+    b2.trans = b3.trans = true;
     b1.tag = "L" + std::to_string(t) + ".b1";
     b2.tag = "L" + std::to_string(t) + ".b2";
     b3.tag = "L" + std::to_string(t) + ".b3";
-    b4.tag = "L" + std::to_string(t) + ".b4";
     for (const auto& c : R.sep) {
       if (!c.comp) continue;
       b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
       b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
     }
-    // w_I -= W x_S: the separator values of every interior are gathered into
-    // one contiguous vector in W's column order, so each row of W (a column
-    // of W^T) is a single dense dot product
+    // x_I = A_II^{-1} v_I - Z x_S (= L^{-T} (L^{-1} v_I - W x_S)), into w_I
+    // and then copied to v_I: the separator values of every interior are
+    // gathered into one contiguous vector in Z's column order, so each row of
+    // Z (a column of Z^T) is a single dense dot product, as is each row of
+    // the symmetric A_II^{-1}
     std::vector<int> gidx;
     std::vector<int64_t> goff(R.in.size());
     for (size_t a = 0; a < R.in.size(); ++a) {
@@ -1782,10 +1814,13 @@ class FactorImpl final : public FactorBase {
       xs = (T*)dev_malloc_async(sizeof(T) * gidx.size() * nr, s);
       P.mem.push_back(xs);
     }
+    std::vector<VecCopyTask> ic;
     for (size_t a = 0; a < R.in.size(); ++a) {
       const auto& r = R.in[a];
-      if (r.s > 0) b3.add(w + nr * lay.vec_off[r.node], r.m, 1, {{r.Wt, r.s, xs + nr * goff[a], nullptr, r.s, false, T(-1)}});
-      b4.add(v + nr * lay.vec_off[r.node], r.m, 0, {{r.Li, r.m, w + nr * lay.vec_off[r.node], nullptr, r.m, true, T(1)}});
+      std::vector<typename GemvList<T>::In> ins = {{r.Ai, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(1)}};
+      if (r.s > 0) ins.push_back({r.Zt, r.s, xs + nr * goff[a], nullptr, r.s, false, T(-1)});
+      b3.add(w + nr * lay.vec_off[r.node], r.m, 0, ins);
+      if (r.m > 0) ic.push_back({nr * (vs + lay.vec_off[r.node]), nr * lay.vec_off[r.node], nr * r.m, 0});
     }
     b1.emit(P, s);
     b2.emit(P, s);
@@ -1799,7 +1834,7 @@ class FactorImpl final : public FactorBase {
       });
     }
     b3.emit(P, s);
-    b4.emit(P, s);
+    veccopy(P, ic, v, v);
   }
 
   // y = A_l x: the factors applied in the opposite order (G^T, B^T up, top
