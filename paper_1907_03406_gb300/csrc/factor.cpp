@@ -554,6 +554,9 @@ struct SepRec {
   bool comp;
   int64_t dst;      // offset of the kept part in the next level vector
   T *L, *Li, *Q1;   // compressed only
+  // for the apply (compressed only): Qf = L_B^{-T} Q1 (m x k), its transpose
+  // Qft (k x m) and Ab = L_B^{-T} L_B^{-1} = B^{-1} (m x m), column-major
+  T *Qf, *Qft, *Ab;
 };
 
 template <typename T>
@@ -1546,6 +1549,7 @@ class FactorImpl final : public FactorBase {
         sr.comp = comp[C];
         sr.dst = layn.vec_off[parent[C]] + oc[C];
         sr.L = sr.Li = sr.Q1 = nullptr;
+        sr.Qf = sr.Qft = sr.Ab = nullptr;
         if (comp[C]) {
           const int e = eidx[C];
           sr.L = Dw + o_mm[e];
@@ -1558,13 +1562,19 @@ class FactorImpl final : public FactorBase {
       // L^{-1} blocks at this point).  Interiors: the apply uses, instead of
       // L^{-1} and W, Z = L^{-T} W = A_II^{-1} A_IS, its transpose and
       // A_II^{-1} = L^{-T} L^{-1} (the same bytes in all, but only dense
-      // blocks); L^{-1} is freed.  Compressed separators: L_B^{-1} mirrored.
+      // blocks); their L^{-1} is freed.  Compressed separators likewise:
+      // Qf = L_B^{-T} Q1, its transpose and B^{-1} = L_B^{-T} L_B^{-1}.
       {
         int64_t zs = 0, as = 0;
         for (const auto& r : rec.in) {
           zs += (int64_t)r.m * r.s;
           as += (int64_t)r.m * r.m;
         }
+        for (const auto& sr : rec.sep)
+          if (sr.comp) {
+            zs += (int64_t)sr.m * sr.k;
+            as += (int64_t)sr.m * sr.m;
+          }
         T* Zb = dalloc<T>(keep_, zs, s, false);
         T* Ztb = dalloc<T>(keep_, zs, s, false);
         T* Ab = dalloc<T>(keep_, as, s, false);
@@ -1579,27 +1589,41 @@ class FactorImpl final : public FactorBase {
           if (r.s > 0) gz.add_lowtri_t(r.Z, r.m, r.m, r.s, r.Li, r.m, r.W, r.m);
           gz.add_lowtri_t(r.Ai, r.m, r.m, r.m, r.Li, r.m, r.Li, r.m);
         }
+        for (auto& sr : rec.sep) {
+          if (!sr.comp) continue;
+          sr.Qf = Zb + oz;
+          sr.Qft = Ztb + oz;
+          sr.Ab = Ab + oa;
+          oz += (int64_t)sr.m * sr.k;
+          oa += (int64_t)sr.m * sr.m;
+          if (sr.k > 0) gz.add_lowtri_t(sr.Qf, sr.m, sr.m, sr.k, sr.Li, sr.m, sr.Q1, sr.m);
+          gz.add_lowtri_t(sr.Ab, sr.m, sr.m, sr.m, sr.Li, sr.m, sr.Li, sr.m);
+        }
         gz.emit(b, s);
         b.run(s);
         CopyList<T, T> cm;
         for (auto& r : rec.in)
           if (r.s > 0) cm.add(r.Z, r.m, r.Zt, r.s, r.s, r.m, kCopyT);
         for (const auto& sr : rec.sep)
-          if (sr.comp) add_mirror(cm, sr.Li, sr.m);
+          if (sr.comp && sr.k > 0) cm.add(sr.Qf, sr.m, sr.Qft, sr.k, sr.k, sr.m, kCopyT);
         cm.emit(b, s);
         b.run(s);
-        // the interiors' L^{-1} blocks are not read again
-        auto it = std::find(keep_.begin(), keep_.end(), (void*)LiI);
-        if (it != keep_.end()) {
-          keep_.erase(it);
-          dev_free_async(LiI, s);
+        // the L^{-1} blocks of interiors and compressed separators are not
+        // read again
+        for (T* li : {LiI, LiB}) {
+          auto it = std::find(keep_.begin(), keep_.end(), (void*)li);
+          if (it != keep_.end()) {
+            keep_.erase(it);
+            dev_free_async(li, s);
+          }
         }
         for (auto& r : rec.in) r.Li = nullptr;
+        for (auto& sr : rec.sep) sr.Li = nullptr;
       }
       int64_t bytes = 0;
       for (const auto& r : rec.in) bytes += ((int64_t)2 * r.m * r.m + (int64_t)3 * r.m * r.s) * sizeof(T);
       for (const auto& r : rec.sep)
-        if (r.comp) bytes += ((int64_t)2 * r.m * r.m + (int64_t)r.m * r.k) * sizeof(T);
+        if (r.comp) bytes += ((int64_t)2 * r.m * r.m + (int64_t)3 * r.m * r.k) * sizeof(T);
       ls.bytes = bytes;
       stats.push_back(ls);
       lev_.push_back(std::move(rec));
@@ -1724,14 +1748,12 @@ class FactorImpl final : public FactorBase {
     T* v = base(t);
     T* w = v + vs * nr;
     T* kp = v + 2 * vs * nr;
-    // every large product is a column dot product: Z^T x through the
-    // columns of Z (v_S -= A_SI A_II^{-1} v_I = W^T L^{-1} v_I), then for the
-    // compressed separators L_B^{-1} x through the mirrored upper triangle
-    // and Q1^T x
-    GemvList<T> f2(nr), f3(nr), f4(nr);
-    f2.trans = f3.trans = f4.trans = true;
+    // every product is a column dot product: Z^T x through the columns of
+    // Z (v_S -= A_SI A_II^{-1} v_I = W^T L^{-1} v_I), then for the
+    // compressed separators Qf^T x (= Q1^T L_B^{-1} v_B)
+    GemvList<T> f2(nr), f4(nr);
+    f2.trans = f4.trans = true;
     f2.tag = "L" + std::to_string(t) + ".f2";
-    f3.tag = "L" + std::to_string(t) + ".f3";
     f4.tag = "L" + std::to_string(t) + ".f4";
     auto si = sep_interiors(R, (int)lay.m.size());
     for (int S = 0; S < (int)si.size(); ++S) {
@@ -1745,12 +1767,9 @@ class FactorImpl final : public FactorBase {
     }
     for (const auto& c : R.sep) {
       if (!c.comp) continue;
-      f3.add(w + nr * lay.vec_off[c.node], c.m, 0,
-             {{c.Li, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1), true}});
-      f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Q1, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
+      f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Qf, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
     }
     f2.emit(P, s);
-    f3.emit(P, s);
     f4.emit(P, s);
     std::vector<VecCopyTask> vc;
     for (const auto& c : R.sep)
@@ -1785,15 +1804,22 @@ class FactorImpl final : public FactorBase {
     for (const auto& c : R.sep)
       if (!c.comp && c.k > 0) vc.push_back({nr * c.dst, nr * lay.vec_off[c.node], nr * c.k, 0});
     veccopy(P, vc, vn, v);
-    GemvList<T> b1(nr), b2(nr), b3(nr);
+    // compressed separators: x_B = B^{-1} v_B + Qf (vn - kp) (= L_B^{-T}
+    // (L_B^{-1} v_B + Q1 (vn - kp))), one dense phase of column dot products
+    // (B^{-1} is symmetric; the rows of Qf are the columns of Qf^T), into w_B
+    GemvList<T> b2(nr), b3(nr);
     b2.trans = b3.trans = true;
-    b1.tag = "L" + std::to_string(t) + ".b1";
     b2.tag = "L" + std::to_string(t) + ".b2";
     b3.tag = "L" + std::to_string(t) + ".b3";
+    std::vector<char> in_w(lay.m.size(), 0);   // nodes whose result sits in w until the final copy
+    std::vector<VecCopyTask> ic;
     for (const auto& c : R.sep) {
       if (!c.comp) continue;
-      b1.add(w + nr * lay.vec_off[c.node], c.m, 1, {{c.Q1, c.m, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)}});
-      b2.add(v + nr * lay.vec_off[c.node], c.m, 0, {{c.Li, c.m, w + nr * lay.vec_off[c.node], nullptr, c.m, true, T(1)}});
+      std::vector<typename GemvList<T>::In> ins = {{c.Ab, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}};
+      if (c.k > 0) ins.push_back({c.Qft, c.k, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)});
+      b2.add(w + nr * lay.vec_off[c.node], c.m, 0, ins);
+      in_w[c.node] = 1;
+      if (c.m > 0) ic.push_back({nr * (vs + lay.vec_off[c.node]), nr * lay.vec_off[c.node], nr * c.m, 0});
     }
     // x_I = A_II^{-1} v_I - Z x_S (= L^{-T} (L^{-1} v_I - W x_S)), into w_I
     // and then copied to v_I: the separator values of every interior are
@@ -1807,14 +1833,13 @@ class FactorImpl final : public FactorBase {
       goff[a] = (int64_t)gidx.size();
       gidx.resize(gidx.size() + r.s);
       for (auto [S, col] : r.nb)
-        for (int j = 0; j < lay.m[S]; ++j) gidx[goff[a] + col + j] = (int)(lay.vec_off[S] + j);
+        for (int j = 0; j < lay.m[S]; ++j) gidx[goff[a] + col + j] = (int)((in_w[S] ? vs : 0) + lay.vec_off[S] + j);
     }
     T* xs = nullptr;
     if (!gidx.empty()) {
       xs = (T*)dev_malloc_async(sizeof(T) * gidx.size() * nr, s);
       P.mem.push_back(xs);
     }
-    std::vector<VecCopyTask> ic;
     for (size_t a = 0; a < R.in.size(); ++a) {
       const auto& r = R.in[a];
       std::vector<typename GemvList<T>::In> ins = {{r.Ai, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(1)}};
@@ -1822,7 +1847,6 @@ class FactorImpl final : public FactorBase {
       b3.add(w + nr * lay.vec_off[r.node], r.m, 0, ins);
       if (r.m > 0) ic.push_back({nr * (vs + lay.vec_off[r.node]), nr * lay.vec_off[r.node], nr * r.m, 0});
     }
-    b1.emit(P, s);
     b2.emit(P, s);
     if (!gidx.empty()) {
       const size_t oi = P.b.push(gidx);
