@@ -894,6 +894,7 @@ class FactorImpl final : public FactorBase {
   std::vector<LevelRec<T>> lev_;
   int mtop_ = 0;
   T *Ltop_ = nullptr, *Litop_ = nullptr;
+  T* Atop_ = nullptr;   // the top block's inverse L^{-T} L^{-1}, which the apply reads
   std::vector<T*> vb_;  // per non-top level: [v | w | kept], 3 * vec_size
   T* vtop_ = nullptr;   // [v | w], 2 * mtop
   Program<T> inv_[4], fwd_[4];   // nr = 1, 2, 4, 8 right-hand sides, built on first use
@@ -1109,9 +1110,10 @@ class FactorImpl final : public FactorBase {
         if (mtop_ > 0) run_fronts<T>(F, b, s, st_, lvl);
         b.run(s);
         if (mtop_ > 0) {   // stream ordered after the top factor
-          CopyList<T, T> cm;
-          add_mirror(cm, Litop_, mtop_);
-          cm.emit(b, s);
+          Atop_ = dalloc<T>(keep_, (size_t)mtop_ * mtop_, s, false);
+          GemmList<T> ga;
+          ga.add_lowtri_t(Atop_, mtop_, mtop_, mtop_, Litop_, mtop_, Litop_, mtop_);
+          ga.emit(b, s);
           b.run(s);
         }
         trace(s, lvl, "top factor issued");
@@ -1781,14 +1783,16 @@ class FactorImpl final : public FactorBase {
   void inverse_top(Sink& P, int nr, cudaStream_t s) {
     T* v = vtop_;
     T* w = vtop_ + (size_t)mtop_ * nr;
-    GemvList<T> a(nr), bt(nr);
-    a.trans = bt.trans = true;
-    a.tag = "top.a";
-    bt.tag = "top.b";
-    a.add(w, mtop_, 0, {{Litop_, mtop_, v, nullptr, mtop_, true, T(1), true}});
-    bt.add(v, mtop_, 0, {{Litop_, mtop_, w, nullptr, mtop_, true, T(1)}});
+    GemvList<T> a(nr);
+    a.trans = true;
+    a.tag = "top";
+    // x = A_top^{-1} v (A_top^{-1} = L^{-T} L^{-1} is symmetric: its columns
+    // are its rows), into w, then copied back to v
+    a.add(w, mtop_, 0, {{Atop_, mtop_, v, nullptr, mtop_, false, T(1)}});
     a.emit(P, s);
-    bt.emit(P, s);
+    std::vector<VecCopyTask> c;
+    if (mtop_ > 0) c.push_back({(int64_t)mtop_ * nr, 0, mtop_ * nr, 0});
+    veccopy(P, c, vtop_, vtop_);
   }
 
   template <class Sink>

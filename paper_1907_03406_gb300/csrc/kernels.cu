@@ -1564,12 +1564,15 @@ __global__ void __launch_bounds__(kThreads) k_vgather(const T* __restrict__ src,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_veccopy(const VecCopyTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kThreads) k_veccopy(const VecCopyTask* __restrict__ tasks, int n,
                                                       const T* __restrict__ src, T* __restrict__ dst) {
+  // one task per warp (a node's kept values: tens to hundreds), eight to a block
   pdl_trigger();
-  const VecCopyTask tk = tasks[blockIdx.x];
+  const int t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
   pdl_wait();
-  for (int i = threadIdx.x; i < tk.len; i += kThreads) dst[tk.dst + i] = src[tk.src + i];
+  if (t >= n) return;
+  const VecCopyTask tk = tasks[t];
+  for (int i = threadIdx.x & 31; i < tk.len; i += 32) dst[tk.dst + i] = src[tk.src + i];
 }
 
 // ---------------------------------------------------------------------------
@@ -2159,7 +2162,7 @@ void launch_veccopy(const VecCopyTask* tasks, int n, const T* src, T* dst, cudaS
   }
   if (n <= 0) return;
   ProfScope ps(P_VECCOPY, s);
-  launch_apply_kernel(k_veccopy<T>, (unsigned)n, s, tasks, src, dst);
+  launch_apply_kernel(k_veccopy<T>, (unsigned)((n + kThreads / 32 - 1) / (kThreads / 32)), s, tasks, n, src, dst);
 }
 
 template <typename T>
