@@ -381,7 +381,21 @@ struct GemmList {
       work(ts, c, fl, by);
       const size_t ot = b.push(ts);
       const int n = (int)ts.size();
+      // launch-log description: tiles, their mean output shape and K
+      std::shared_ptr<std::string> note;
+      if (prof_logging()) {
+        double sm = 0, sn = 0, sk = 0;
+        for (const auto& g : ts) {
+          sm += g.M;
+          sn += g.N;
+          for (int q = g.c_begin; q < g.c_begin + g.c_count; ++q) sk += c[q].K;
+        }
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "simt tiles %d mavg %.1f navg %.1f kavg %.0f", n, sm / n, sn / n, sk / n);
+        note = std::make_shared<std::string>(buf);
+      }
       b.launches.push_back([=](const char* d) {
+        if (note) prof_note(note->c_str());
         prof_work(fl, by);
         launch_gemm<T>((const GemmTask<T>*)(d + ot), (const GemmContrib<T>*)(d + oc), n, s);
       });
