@@ -558,7 +558,10 @@ struct InteriorRec {
   T *L, *Li, *W;   // Li: only while the level is factored
   // for the apply: Z = L^{-T} W = A_II^{-1} A_IS (m x s) and its transpose
   // Zt (s x m), and Ai = L^{-T} L^{-1} = A_II^{-1} (m x m), all column-major
+  // with leading dimensions ldm = pad(m), lds = pad(s) (columns start on a
+  // 32-byte sector)
   T *Z, *Zt, *Ai;
+  int ldm, lds;
   std::vector<std::pair<int, int>> nb;  // (separator, column offset in W)
 };
 
@@ -570,7 +573,9 @@ struct SepRec {
   T *L, *Li, *Q1;   // compressed only
   // for the apply (compressed only): Qf = L_B^{-T} Q1 (m x k), its transpose
   // Qft (k x m) and Ab = L_B^{-T} L_B^{-1} = B^{-1} (m x m), column-major
+  // with leading dimensions ldm = pad(m), ldk = pad(k)
   T *Qf, *Qft, *Ab;
+  int ldm, ldk;
 };
 
 template <typename T>
@@ -1168,6 +1173,7 @@ class FactorImpl final : public FactorBase {
         r.Li = LiI + li_off[i];
         r.W = Wb + w_off[i];
         r.Z = r.Zt = r.Ai = nullptr;
+        r.ldm = r.lds = 0;
         for (int k = lay.up_ptr[i]; k < lay.up_ptr[i + 1]; ++k) r.nb.push_back({lay.up_nb[k], lay.up_col[k]});
         rec.in.push_back(r);
       }
@@ -1566,6 +1572,7 @@ class FactorImpl final : public FactorBase {
         sr.dst = layn.vec_off[parent[C]] + oc[C];
         sr.L = sr.Li = sr.Q1 = nullptr;
         sr.Qf = sr.Qft = sr.Ab = nullptr;
+        sr.ldm = sr.ldk = 0;
         if (comp[C]) {
           const int e = eidx[C];
           sr.L = Dw + o_mm[e];
@@ -1581,47 +1588,59 @@ class FactorImpl final : public FactorBase {
       // blocks); their L^{-1} is freed.  Compressed separators likewise:
       // Qf = L_B^{-T} Q1, its transpose and B^{-1} = L_B^{-T} L_B^{-1}.
       {
-        int64_t zs = 0, as = 0;
-        for (const auto& r : rec.in) {
-          zs += (int64_t)r.m * r.s;
-          as += (int64_t)r.m * r.m;
+        // leading dimensions rounded up to a 32-byte sector, so that every
+        // column the apply reads starts on one
+        constexpr int kApplyPad = 32 / (int)sizeof(T);   // elements per 32-byte sector
+        auto pad = [](int x) { return (x + kApplyPad - 1) / kApplyPad * kApplyPad; };
+        int64_t zs = 0, zts = 0, as = 0;
+        for (auto& r : rec.in) {
+          r.ldm = pad(r.m);
+          r.lds = pad(r.s);
+          zs += (int64_t)r.ldm * r.s;
+          zts += (int64_t)r.lds * r.m;
+          as += (int64_t)r.ldm * r.m;
         }
-        for (const auto& sr : rec.sep)
+        for (auto& sr : rec.sep)
           if (sr.comp) {
-            zs += (int64_t)sr.m * sr.k;
-            as += (int64_t)sr.m * sr.m;
+            sr.ldm = pad(sr.m);
+            sr.ldk = pad(sr.k);
+            zs += (int64_t)sr.ldm * sr.k;
+            zts += (int64_t)sr.ldk * sr.m;
+            as += (int64_t)sr.ldm * sr.m;
           }
         T* Zb = dalloc<T>(keep_, zs, s, false);
-        T* Ztb = dalloc<T>(keep_, zs, s, false);
+        T* Ztb = dalloc<T>(keep_, zts, s, false);
         T* Ab = dalloc<T>(keep_, as, s, false);
         GemmList<T> gz;
-        int64_t oz = 0, oa = 0;
+        int64_t oz = 0, ozt = 0, oa = 0;
         for (auto& r : rec.in) {
           r.Z = Zb + oz;
-          r.Zt = Ztb + oz;
+          r.Zt = Ztb + ozt;
           r.Ai = Ab + oa;
-          oz += (int64_t)r.m * r.s;
-          oa += (int64_t)r.m * r.m;
-          if (r.s > 0) gz.add_lowtri_t(r.Z, r.m, r.m, r.s, r.Li, r.m, r.W, r.m);
-          gz.add_lowtri_t(r.Ai, r.m, r.m, r.m, r.Li, r.m, r.Li, r.m);
+          oz += (int64_t)r.ldm * r.s;
+          ozt += (int64_t)r.lds * r.m;
+          oa += (int64_t)r.ldm * r.m;
+          if (r.s > 0) gz.add_lowtri_t(r.Z, r.ldm, r.m, r.s, r.Li, r.m, r.W, r.m);
+          gz.add_lowtri_t(r.Ai, r.ldm, r.m, r.m, r.Li, r.m, r.Li, r.m);
         }
         for (auto& sr : rec.sep) {
           if (!sr.comp) continue;
           sr.Qf = Zb + oz;
-          sr.Qft = Ztb + oz;
+          sr.Qft = Ztb + ozt;
           sr.Ab = Ab + oa;
-          oz += (int64_t)sr.m * sr.k;
-          oa += (int64_t)sr.m * sr.m;
-          if (sr.k > 0) gz.add_lowtri_t(sr.Qf, sr.m, sr.m, sr.k, sr.Li, sr.m, sr.Q1, sr.m);
-          gz.add_lowtri_t(sr.Ab, sr.m, sr.m, sr.m, sr.Li, sr.m, sr.Li, sr.m);
+          oz += (int64_t)sr.ldm * sr.k;
+          ozt += (int64_t)sr.ldk * sr.m;
+          oa += (int64_t)sr.ldm * sr.m;
+          if (sr.k > 0) gz.add_lowtri_t(sr.Qf, sr.ldm, sr.m, sr.k, sr.Li, sr.m, sr.Q1, sr.m);
+          gz.add_lowtri_t(sr.Ab, sr.ldm, sr.m, sr.m, sr.Li, sr.m, sr.Li, sr.m);
         }
         gz.emit(b, s);
         b.run(s);
         CopyList<T, T> cm;
         for (auto& r : rec.in)
-          if (r.s > 0) cm.add(r.Z, r.m, r.Zt, r.s, r.s, r.m, kCopyT);
+          if (r.s > 0) cm.add(r.Z, r.ldm, r.Zt, r.lds, r.s, r.m, kCopyT);
         for (const auto& sr : rec.sep)
-          if (sr.comp && sr.k > 0) cm.add(sr.Qf, sr.m, sr.Qft, sr.k, sr.k, sr.m, kCopyT);
+          if (sr.comp && sr.k > 0) cm.add(sr.Qf, sr.ldm, sr.Qft, sr.ldk, sr.k, sr.m, kCopyT);
         cm.emit(b, s);
         b.run(s);
         // the L^{-1} blocks of interiors and compressed separators are not
@@ -1777,13 +1796,13 @@ class FactorImpl final : public FactorBase {
       std::vector<typename GemvList<T>::In> ins;
       for (auto [a, col] : si[S]) {
         const auto& r = R.in[a];
-        ins.push_back({r.Z + (size_t)col * r.m, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
+        ins.push_back({r.Z + (size_t)col * r.ldm, r.ldm, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(-1)});
       }
       f2.add(v + nr * lay.vec_off[S], lay.m[S], 1, ins);
     }
     for (const auto& c : R.sep) {
       if (!c.comp) continue;
-      f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Qf, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
+      f4.add(kp + nr * lay.vec_off[c.node], c.k, 0, {{c.Qf, c.ldm, v + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}});
     }
     f2.emit(P, s);
     f4.emit(P, s);
@@ -1833,8 +1852,8 @@ class FactorImpl final : public FactorBase {
     std::vector<VecCopyTask> ic;
     for (const auto& c : R.sep) {
       if (!c.comp) continue;
-      std::vector<typename GemvList<T>::In> ins = {{c.Ab, c.m, v + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}};
-      if (c.k > 0) ins.push_back({c.Qft, c.k, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)});
+      std::vector<typename GemvList<T>::In> ins = {{c.Ab, c.ldm, v + nr * lay.vec_off[c.node], nullptr, c.m, false, T(1)}};
+      if (c.k > 0) ins.push_back({c.Qft, c.ldk, vn + nr * c.dst, kp + nr * lay.vec_off[c.node], c.k, false, T(1)});
       b2.add(w + nr * lay.vec_off[c.node], c.m, 0, ins);
       in_w[c.node] = 1;
       if (c.m > 0) ic.push_back({nr * (vs + lay.vec_off[c.node]), nr * lay.vec_off[c.node], nr * c.m, 0});
@@ -1860,8 +1879,8 @@ class FactorImpl final : public FactorBase {
     }
     for (size_t a = 0; a < R.in.size(); ++a) {
       const auto& r = R.in[a];
-      std::vector<typename GemvList<T>::In> ins = {{r.Ai, r.m, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(1)}};
-      if (r.s > 0) ins.push_back({r.Zt, r.s, xs + nr * goff[a], nullptr, r.s, false, T(-1)});
+      std::vector<typename GemvList<T>::In> ins = {{r.Ai, r.ldm, v + nr * lay.vec_off[r.node], nullptr, r.m, false, T(1)}};
+      if (r.s > 0) ins.push_back({r.Zt, r.lds, xs + nr * goff[a], nullptr, r.s, false, T(-1)});
       b3.add(w + nr * lay.vec_off[r.node], r.m, 0, ins);
       if (r.m > 0) ic.push_back({nr * (vs + lay.vec_off[r.node]), nr * lay.vec_off[r.node], nr * r.m, 0});
     }

@@ -1510,9 +1510,48 @@ __global__ void __launch_bounds__(kThreads, NR <= 2 ? 4 : 2)
       const T* a = cb.A + (size_t)w * cb.lda;
       const size_t cstep = (size_t)kWarps * cb.lda;
       const int cmin = cb.tri ? cb.tri - 1 + w : 0;   // absolute column of u = 0
+      int is = i0;   // first row of the scalar loop below
+      if constexpr (sizeof(T) == 4) {
+        // a dense contribution whose columns start on 16 bytes (the apply's
+        // blocks have padded leading dimensions) and whose rows start on a
+        // multiple of 4: lane l reads rows i0 + 4 l .. + 3 of each column with
+        // one 16-byte load, then 128 rows on; the rest (< 4 rows) is scalar.
+        // The choice does not depend on NR, so every NR sums in one order.
+        if (!cb.tri && (i0 & 3) == 0 && (cb.lda & 3) == 0 && (reinterpret_cast<uintptr_t>(cb.A) & 15) == 0) {
+          const int iv1 = i0 + ((i1 - i0) & ~3);
+          constexpr int kVecUnroll = CW * NR <= 4 ? 2 : 1;
+#pragma unroll kVecUnroll
+          for (int i = i0 + 4 * lane; i < iv1; i += 128) {
+            float xv[4][NR];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+              for (int q = 0; q < NR; ++q) {
+                float v = cb.x[(size_t)(i + e) * NR + q];
+                if (cb.x2) v -= cb.x2[(size_t)(i + e) * NR + q];
+                xv[e][q] = cb.alpha * v;
+              }
+            float4 av[CW];
+#pragma unroll
+            for (int u = 0; u < CW; ++u)
+              av[u] = w + kWarps * u < tk.M ? *reinterpret_cast<const float4*>(a + u * cstep + i)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < CW; ++u)
+#pragma unroll
+              for (int q = 0; q < NR; ++q) {
+                acc[u][q] = fma(av[u].x, xv[0][q], acc[u][q]);
+                acc[u][q] = fma(av[u].y, xv[1][q], acc[u][q]);
+                acc[u][q] = fma(av[u].z, xv[2][q], acc[u][q]);
+                acc[u][q] = fma(av[u].w, xv[3][q], acc[u][q]);
+              }
+          }
+          is = iv1;
+        }
+      }
       constexpr int kUnroll = (sizeof(T) == 4 && NR <= 2 && CW <= 4) ? 4 : 2;   // row steps in flight
 #pragma unroll kUnroll
-      for (int i = i0 + lane; i < i1; i += 32) {
+      for (int i = is + lane; i < i1; i += 32) {
         T xv[NR];
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
