@@ -325,6 +325,15 @@ struct GemmList {
       add(C + i0, ldc, std::min(tm, M - i0), N, T(1), 0, {{Li + i0, ldli, false, B, ldb, false, K}});
     }
   }
+  // C = Li^T Li (M x M, symmetric) with Li lower triangular: for each row
+  // band only the column tiles up to and including the diagonal (its lower
+  // part; the caller mirrors the upper triangle from it)
+  void add_lowtri_tt_lower(T* C, int ldc, int M, const T* Li, int ldli) {
+    const int tm = use_tc(M, M) ? kTileTC : kTile;
+    for (int i0 = 0; i0 < M; i0 += tm)
+      add(C + i0, ldc, std::min(tm, M - i0), std::min(M, i0 + tm), T(1), 0,
+          {{Li + i0 + (size_t)i0 * ldli, ldli, true, Li + i0, ldli, false, M - i0}});
+  }
   // C[M x N] = Li^T B with Li lower triangular (M x M): the row band starting
   // at i0 needs only rows i0.. of B (column i0 + r of Li is zero above row
   // i0 + r)
@@ -444,12 +453,13 @@ struct CopyList {
 // contiguously as column i (the apply reads both L^{-1} x and L^{-T} x as
 // column dot products).  Only once the factor no longer needs the zeros.
 template <typename T>
-void add_mirror(CopyList<T, T>& cl, T* Li, int m) {
+void add_mirror(CopyList<T, T>& cl, T* Li, int m, int ld = 0) {
+  if (ld <= 0) ld = m;
   for (int j0 = 0; j0 < m; j0 += kTile)
     for (int i0 = 0; i0 <= j0; i0 += kTile) {
       const int ni = std::min(kTile, m - i0), nj = std::min(kTile, m - j0);
-      if (i0 == j0) cl.add(Li + i0 + (size_t)i0 * m, m, Li + i0 + (size_t)i0 * m, m, ni, ni, kMirror);
-      else cl.add(Li + j0 + (size_t)i0 * m, m, Li + i0 + (size_t)j0 * m, m, ni, nj, kCopyT);
+      if (i0 == j0) cl.add(Li + i0 + (size_t)i0 * ld, ld, Li + i0 + (size_t)i0 * ld, ld, ni, ni, kMirror);
+      else cl.add(Li + j0 + (size_t)i0 * ld, ld, Li + i0 + (size_t)j0 * ld, ld, ni, nj, kCopyT);
     }
 }
 
@@ -1131,8 +1141,12 @@ class FactorImpl final : public FactorBase {
         if (mtop_ > 0) {   // stream ordered after the top factor
           Atop_ = dalloc<T>(keep_, (size_t)mtop_ * mtop_, s, false);
           GemmList<T> ga;
-          ga.add_lowtri_t(Atop_, mtop_, mtop_, mtop_, Litop_, mtop_, Litop_, mtop_);
+          ga.add_lowtri_tt_lower(Atop_, mtop_, mtop_, Litop_, mtop_);
           ga.emit(b, s);
+          b.run(s);
+          CopyList<T, T> cm;
+          add_mirror(cm, Atop_, mtop_);
+          cm.emit(b, s);
           b.run(s);
         }
         trace(s, lvl, "top factor issued");
@@ -1621,7 +1635,7 @@ class FactorImpl final : public FactorBase {
           ozt += (int64_t)r.lds * r.m;
           oa += (int64_t)r.ldm * r.m;
           if (r.s > 0) gz.add_lowtri_t(r.Z, r.ldm, r.m, r.s, r.Li, r.m, r.W, r.m);
-          gz.add_lowtri_t(r.Ai, r.ldm, r.m, r.m, r.Li, r.m, r.Li, r.m);
+          gz.add_lowtri_tt_lower(r.Ai, r.ldm, r.m, r.Li, r.m);
         }
         for (auto& sr : rec.sep) {
           if (!sr.comp) continue;
@@ -1632,15 +1646,20 @@ class FactorImpl final : public FactorBase {
           ozt += (int64_t)sr.ldk * sr.m;
           oa += (int64_t)sr.ldm * sr.m;
           if (sr.k > 0) gz.add_lowtri_t(sr.Qf, sr.ldm, sr.m, sr.k, sr.Li, sr.m, sr.Q1, sr.m);
-          gz.add_lowtri_t(sr.Ab, sr.ldm, sr.m, sr.m, sr.Li, sr.m, sr.Li, sr.m);
+          gz.add_lowtri_tt_lower(sr.Ab, sr.ldm, sr.m, sr.Li, sr.m);
         }
         gz.emit(b, s);
         b.run(s);
         CopyList<T, T> cm;
-        for (auto& r : rec.in)
+        for (auto& r : rec.in) {
           if (r.s > 0) cm.add(r.Z, r.ldm, r.Zt, r.lds, r.s, r.m, kCopyT);
+          add_mirror(cm, r.Ai, r.m, r.ldm);   // the inverses exactly symmetric
+        }
         for (const auto& sr : rec.sep)
-          if (sr.comp && sr.k > 0) cm.add(sr.Qf, sr.ldm, sr.Qft, sr.ldk, sr.k, sr.m, kCopyT);
+          if (sr.comp) {
+            if (sr.k > 0) cm.add(sr.Qf, sr.ldm, sr.Qft, sr.ldk, sr.k, sr.m, kCopyT);
+            add_mirror(cm, sr.Ab, sr.m, sr.ldm);
+          }
         cm.emit(b, s);
         b.run(s);
         // the L^{-1} blocks of interiors and compressed separators are not
