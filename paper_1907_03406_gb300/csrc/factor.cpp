@@ -24,13 +24,20 @@
 //     kept variables, blocks and re-expanded Phi.
 // The top node gets a dense Cholesky (Sec. 4.5).
 //
-// The apply keeps L^{-1} of every eliminated / compressed block so that each
-// step of Sec. 4.7 is a batched matrix-vector product:
+// The steps of Sec. 4.7, written with the triangular factors,
 //  forward:  y_I = L_I^{-1} b_I;  b_S -= W_IS^T y_I;  c_B = L_B^{-1} b_B;
 //            kept_B = Q1_B^T c_B;  gather to the next level
 //  top:      x = L^{-T} L^{-1} b
 //  backward: x_B = L_B^{-T} (c_B + Q1_B (x_kept - kept_B));
 //            x_I = L_I^{-T} (y_I - sum_S W_IS x_S)
+// are applied through dense blocks formed at the end of each level, Z =
+// L_I^{-T} W_IS = A_II^{-1} A_IS, A_II^{-1}, Qf = L_B^{-T} Q1_B, B^{-1} =
+// L_B^{-T} L_B^{-1} and A_top^{-1}, each step one batched matrix-vector
+// product of dense blocks (the same bytes, no triangular phases):
+//  forward:  b_S -= Z^T b_I;  kept_B = Qf^T b_B;  gather to the next level
+//  top:      x = A_top^{-1} b
+//  backward: x_B = B^{-1} b_B + Qf (x_kept - kept_B);
+//            x_I = A_II^{-1} b_I - sum_S Z x_S
 // The Q2 part of a compressed node is its decoupled identity block (Eq. (M')):
 // its forward value Q2^T c_B comes back unchanged, which is what
 // c_B - Q1 Q1^T c_B restores.
@@ -448,10 +455,9 @@ struct CopyList {
   }
 };
 
-// Upper triangle of a lower-triangular m x m block (ld m) <- the transpose of
-// its lower triangle, so that row i of the lower factor is also available
-// contiguously as column i (the apply reads both L^{-1} x and L^{-T} x as
-// column dot products).  Only once the factor no longer needs the zeros.
+// Upper triangle of an m x m block (leading dimension ld, m by default) <-
+// the transpose of its lower triangle: makes the symmetric inverses the
+// apply reads exactly symmetric after only their lower part was formed.
 template <typename T>
 void add_mirror(CopyList<T, T>& cl, T* Li, int m, int ld = 0) {
   if (ld <= 0) ld = m;
