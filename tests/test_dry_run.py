@@ -69,6 +69,10 @@ CASES = [
     [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "fp64", "nest_all_all",
      {"gemv_min_elems": 65536, "gemv_max_elems": 1 << 20, "front_small": 512, "tensor_cores": 1}],
     [[37, 29, 23], 3, "7pt_fv_3d", 1, 8, 2, "mixed", "nest_all_all", {"tensor_cores": 2, "tc_min_dim": 1}],
+    # the bench's recipe at realistic sizes (many levels, thousands of
+    # compressed separators, the padded apply blocks)
+    [[64, 64, 64], 3, "7pt_fv_3d", 1, 8, 2, "mixed", "nest_all_all"],
+    [[48, 48, 48], 3, "7pt_fv_3d", 1, 8, 2, "fp64", "nest_all_all"],
     [[24, 25, 25], 3, "q1_elastic_3d", 1, 8, 1, "mixed", "nest_all_all", {"tensor_cores": 1, "tc_min_dim": 200}],
 ]
 
